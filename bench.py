@@ -1,0 +1,349 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: RHS solves/s at 1e-8 true relative residual.
+
+One step = one pass of the whole path on one synthetic problem: device mesh
+and block pattern, assembly of Eq. 4 into 3x3-block rows (+ block-Jacobi
+inverse + complex64 copy), plane-wave right-hand side, and the mixed-precision
+COCG solve with FP64 refinement down to ||b - A x|| / ||b|| <= 1e-8.
+Default workload: the 3-wavelength cube (30^3 elements of lambda/10 at 3 GHz,
+centred 6^3 PEC cube, eps_r = 4 slab, 88 998 unknowns), one plane wave.
+
+`value` times steps with inputs resident in HBM (material grid on the device,
+solution left on the device); `e2e` runs the same steps through the public
+API with host buffers (host material grid in, host solution out).  Between
+timed steps a 512 MiB buffer is written to flush the 126 MB L2.
+
+--impl reference times the FP64 CPU oracle on the host cores (bounded sample,
+see cpu_baseline).  Under torchrun every rank solves its own copy of the
+problem (independent problems, no data exchange): "scaling": "weak".
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+WORKLOADS = ("config2", "config1", "config3", "config4")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="config2", choices=WORKLOADS)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload(name):
+    from paper_0704_2344_gb300 import workloads as W
+    return {"config1": W.config1, "config2": W.config2, "config3": W.config3, "config4": W.config4}[name]()
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [v.strip() for v in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx.append(float(p[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def algorithmic_bytes(info, inner_iters, passes, R=1):
+    """Bytes the method must move per persistent solve launch (complex64
+    inner loop, FP64 refinement), at R right-hand sides:
+      inner iteration: complex64 matrix nnzb*(9*8 + 4) + row pointers, the
+        block-Jacobi inverse n*9*8, and 12 vector passes of n_dof*R*8 B
+        (SpMV: p in, q out; update: p, q, d, r in, d, r, z out; p = z + beta p:
+        z, p in, p out);
+      refinement pass: complex128 matrix nnzb*(9*16 + 4) + row pointers,
+        x and b in, r out (3 * 16 B per dof and column), inner start (r64 in,
+        r, z, p, d out: 16 + 4*8 B), block inverse, x update (d in, x in/out:
+        8 + 32 B)."""
+    nnzb, n, n_dof = info["nnzb"], info["n_nodes"], info["n_dof"]
+    ptr = (n + 1) * 4
+    inner = nnzb * (9 * 8 + 4) + ptr + n * 72 + 12 * n_dof * R * 8
+    outer = nnzb * (9 * 16 + 4) + ptr + n * 72 + n_dof * R * (48 + 48 + 40)
+    return inner_iters * inner / max(R, 1) * R + passes * outer, inner, outer
+
+
+def run_ours(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+
+    from paper_0704_2344_gb300 import build, fe
+    build.build()
+    torch.cuda.set_device(local_rank)
+    prob, waves = workload(args.workload)
+    precision = fe.FE_PREC_MIXED if args.precision == "mixed" else fe.FE_PREC_FP64
+    stream = torch.cuda.Stream()
+    ctx = fe.fe_ctx_create(local_rank, stream=stream.cuda_stream)
+    opts = fe.solve_opts(precision=precision, tol=1e-8)
+    mat_d = torch.from_numpy(np.ascontiguousarray(prob.material).ravel()).to(f"cuda:{local_rank}")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
+    R = waves.count
+
+    def step(device_inputs=True, x_host=None, x_dev=None):
+        mesh = fe.fe_mesh_create_from(ctx, prob, material_device_ptr=mat_d.data_ptr() if device_inputs else None)
+        try:
+            system = fe.fe_assemble(ctx, mesh, prob.freq_hz, precision)
+            try:
+                n_dof = fe.fe_mesh_info(mesh)["n_dof"]
+                if device_inputs:
+                    st, _, rep = fe.fe_solve_batch(ctx, system, waves, n_dof, opts, x_out=x_dev.data_ptr(),
+                                                   x_on_device=True, raise_on_fail=False)
+                else:
+                    st, _, rep = fe.fe_solve_batch(ctx, system, waves, n_dof, opts, x_out=x_host,
+                                                   raise_on_fail=False)
+                stats = fe.fe_last_solve_stats(ctx)
+            finally:
+                fe.fe_system_destroy(system)
+        finally:
+            fe.fe_mesh_destroy(mesh)
+        return st, rep, stats
+
+    mesh0 = fe.fe_mesh_create_from(ctx, prob)
+    info = fe.fe_mesh_info(mesh0)
+    fe.fe_mesh_destroy(mesh0)
+    x_dev = torch.empty((info["n_dof"], R), dtype=torch.complex128, device=f"cuda:{local_rank}")
+    x_host = np.empty((info["n_dof"], R), dtype=np.complex128)
+    for _ in range(args.warmup):
+        step(True, x_dev=x_dev)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    launches0 = fe.fe_launch_count()
+    evs = []
+    kernel_ms = 0.0
+    inner_iters = passes = 0
+    statuses = []
+    t_wall0 = time.perf_counter()
+    with ClockSampler(local_rank) as clk:
+        for k in range(args.steps):
+            flush.fill_(k & 255)  # L2 flush, outside the timed events
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, rep, stats = step(True, x_dev=x_dev)
+            e1.record(stream)
+            evs.append((e0, e1))
+            kernel_ms += stats["kernel_ms"]
+            inner_iters += stats["inner_iters"]
+            passes += stats["passes"]
+            statuses.append((st, [r["rel_residual"] for r in rep], [r["iterations"] for r in rep]))
+        torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall0
+    launches = fe.fe_launch_count() - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in evs)
+    # end to end through the public API with host buffers
+    e2e_ms = []
+    for k in range(max(1, min(args.steps, 3))):
+        flush.fill_(k & 255)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        step(False, x_host=x_host)
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    ms_local = total_ms / args.steps
+    ms = ms_local
+    if world > 1:
+        t = torch.tensor([ms_local], device=f"cuda:{local_rank}", dtype=torch.float64)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    alg, inner_b, outer_b = algorithmic_bytes(info, inner_iters, passes, R)
+    achieved = alg / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else None
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    fe.fe_ctx_destroy(ctx)
+    ok = all(s[0] == 0 for s in statuses)
+    value = world * R * 1e3 / ms
+    line = {
+        "metric": "RHS solves/s at 1e-8 rel. residual",
+        "value": round(value, 4),
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64+f64" if precision == fe.FE_PREC_MIXED else "c128",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {prob.name}, {info['n_dof']} unknowns, {R} plane wave(s)",
+                   "n_dof": info["n_dof"], "nnzb": info["nnzb"], "rhs": R, "precision": args.precision,
+                   "tol": 1e-8, "l2": "512 MiB flush between timed steps", "parallelism": f"replicas x{world}"},
+        "converged": ok,
+        "iterations_per_solve": inner_iters / (args.steps * R),
+        "refinement_passes_per_solve": passes / args.steps,
+        "final_rel_residual": max(max(s[1]) for s in statuses),
+        "e2e": {"value": round(world * R * 1e3 / statistics.median(e2e_ms), 4), "unit": "solves/s",
+                "h2d_bytes_per_step": int(prob.material.size + 16 * 2 * len(prob.eps_r) + 56 * R),
+                "d2h_bytes_per_step": int(info["n_dof"] * R * 16)},
+        "roofline": {"kernel": "k_solve (persistent refinement + COCG)", "bound": "hbm",
+                     "achieved": round(achieved, 1) if achieved else None, "peak": peak,
+                     "unit": "GB/s", "frac": round(achieved / peak, 4) if achieved else None,
+                     "peak_source": peak_src, "traffic": None,
+                     "algorithmic_bytes_per_launch": int(alg / args.steps),
+                     "launch_ms": round(kernel_ms / args.steps, 4),
+                     "kernel_share_of_step": round(kernel_ms / total_ms, 4) if total_ms else None},
+        "gpu_launches": launches,
+        "wall_s_timed": round(t_wall, 3),
+    }
+    line["clocks"] = clk.summary()
+    return line
+
+
+def cpu_baseline(args, sample_s):
+    """The oracle as it stands on the host cores (single thread): its
+    assembly + right-hand side of the same workload, then its block-Jacobi
+    COCG for a bounded time; the solve time is extrapolated from the measured
+    time per iteration to the oracle COCG's own iteration count when that is
+    known (stored by tests/golden/make_reference.py), else reported per
+    iteration only."""
+    import numpy as np
+
+    from oracle import fem, krylov
+    prob, waves = workload(args.workload)
+    t0 = time.perf_counter()
+    maps = fem.mesh_maps(prob)
+    A = fem.assemble(prob, maps=maps)
+    B = fem.rhs(prob, waves, maps=maps)
+    Dinv = krylov.block_jacobi_inverse(A)
+    t_setup = time.perf_counter() - t0
+    t1 = time.perf_counter()
+    it = 0
+    budget = max(1.0, sample_s - t_setup)
+    x, it_done, _ = krylov.cocg(A, B[:, 0], tol=1e-8, maxiter=50, Dinv=Dinv)
+    it += max(it_done, 1)
+    while time.perf_counter() - t1 < budget and it_done == 50:
+        x, it_done, _ = krylov.cocg(A, B[:, 0], tol=1e-8, maxiter=50, Dinv=Dinv, x0=x)
+        it += max(it_done, 1)
+    t_iter = (time.perf_counter() - t1) / it
+    ref = ROOT / "tests" / "golden" / f"{args.workload}_x.npz"
+    n_it = None
+    if ref.exists():
+        with np.load(ref) as z:
+            if "cocg_iterations" in z:
+                n_it = int(z["cocg_iterations"])
+    cores = 1
+    if n_it:
+        solve_s = t_setup + n_it * t_iter * waves.count
+        value = waves.count / solve_s
+        sample = (f"oracle mesh+assembly+rhs ({t_setup:.1f} s) and {it} block-Jacobi COCG iterations "
+                  f"({t_iter * 1e3:.2f} ms each), extrapolated to the oracle's {n_it} iterations to 1e-8")
+    else:
+        value = None
+        sample = (f"oracle mesh+assembly+rhs ({t_setup:.1f} s) and {it} block-Jacobi COCG iterations "
+                  f"({t_iter * 1e3:.2f} ms each); iterations to 1e-8 unknown")
+    return {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": sample,
+            "setup_s": round(t_setup, 3), "ms_per_iteration": round(t_iter * 1e3, 3),
+            "cpu_count": os.cpu_count()}
+
+
+def main():
+    args = parse()
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ.setdefault(v, "1")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        t0 = time.perf_counter()
+        for _ in range(args.warmup):
+            pass
+        steps = []
+        cb = None
+        for _ in range(args.steps):
+            cb = cpu_baseline(args, args.cpu_sample_s / max(1, args.steps))
+            steps.append(cb)
+        val = cb["value"]
+        line = {"impl": "reference", "metric": "RHS solves/s at 1e-8 rel. residual", "value": val,
+                "unit": "solves/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "higher_is_better": True, "data": "synthetic", "config": {"workload": args.workload},
+                "cpu_baseline": cb,
+                "e2e": {"value": val, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "wall_s": round(time.perf_counter() - t0, 2)}
+        print(json.dumps(line), flush=True)
+        return
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    line = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            line["cpu_baseline"] = cpu_baseline(args, args.cpu_sample_s)
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

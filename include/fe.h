@@ -1,0 +1,249 @@
+/*
+ * fe.h - C ABI of the GB300 nodal finite-element H-field scattering solver.
+ *
+ * The library assembles and solves the time-harmonic total-field H
+ * formulation of Vollaire, Nicolas & Nicolas, "Parallel computing for the
+ * finite element method" (Section 2, Eqs. 1-4): curl-curl with 1/eps_r, the
+ * grad-div penalty (Eq. 2), the -k0^2 mu_r mass term, the second-order
+ * Engquist-Majda absorbing condition on the rectangular outer faces (Eq. 3),
+ * PEC surfaces, and the incident plane-wave right-hand side of Eq. 4.
+ * Geometry is a voxel box of first-order (trilinear) hexahedra.  Unknowns are
+ * the three Cartesian H components at every active node ("three lines per
+ * node", Section 3.1.2), stored as a 3x3-block sparse row matrix.
+ *
+ * Conventions used by every call
+ *   - Units SI, time dependence e^{j omega t}, c0 = 299 792 458 m/s,
+ *     k0 = 2 pi f / c0.
+ *   - Element (i,j,k) id = i + nx*(j + ny*k); node (i,j,k) id =
+ *     i + (nx+1)*(j + (ny+1)*k); local node a = ix + 2*iy + 4*iz.
+ *   - Active element: material byte != 255 (255 = PEC, not meshed).
+ *     Active node: touches at least one active element.  Active nodes are
+ *     ranked by increasing node id; dof = 3*rank + component (x, y, z).
+ *   - Block pattern: block (n, m) exists iff nodes n and m share an active
+ *     element; col_idx ascending within each block row, diagonal included.
+ *   - Faces are encoded 6*element + face, face 0..5 = -x, +x, -y, +y, -z, +z,
+ *     listed in ascending order.
+ *   - Complex numbers are interleaved (re, im) pairs: complex128 = two
+ *     doubles, complex64 = two floats.  A block is stored row-major:
+ *     value (alpha, beta) of block s at [9*s + 3*alpha + beta].
+ *   - Multi-right-hand-side vectors are laid out [n_dof][nrhs] (the nrhs
+ *     values of one dof are contiguous).
+ *
+ * Ownership and errors
+ *   - Every opaque handle and every device buffer the library allocates is
+ *     owned by the library and freed by the matching *_destroy call.
+ *   - Caller buffers (host or device) are only read or written during the
+ *     call that receives them; the call returns once they are no longer used
+ *     (device outputs are complete on the context's stream).
+ *   - Every call returns an fe_status.  No exception or abort crosses the
+ *     ABI.  fe_last_error() returns a thread-local message for the last
+ *     failing call of the calling thread.
+ *   - All GPU work of a context runs on the CUDA stream given in fe_options
+ *     (NULL: a stream the context creates).  Calls on one context must not
+ *     overlap in time from different host threads.
+ */
+#ifndef FE_H
+#define FE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum fe_status {
+    FE_OK = 0,
+    FE_PENDING = 1,            /* fe_serve_poll: request not finished yet */
+    FE_ERR_INVALID_ARG = -1,   /* a NULL handle, a size out of range, ... */
+    FE_ERR_MESH = -2,          /* mesh rules broken (PEC or a non-vacuum material on the outer box) */
+    FE_ERR_OOM = -3,           /* a device or host allocation failed, or admission budget exceeded */
+    FE_ERR_BREAKDOWN = -4,     /* Krylov breakdown (p^T A p or r^T z vanished) */
+    FE_ERR_NOT_CONVERGED = -5, /* iteration limits reached above tolerance */
+    FE_ERR_TIMEOUT = -6,       /* a bounded device-side wait (grid barrier) expired */
+    FE_ERR_CUDA = -7,          /* a CUDA runtime call failed */
+    FE_ERR_UNSUPPORTED = -8    /* option combination not built */
+} fe_status;
+
+typedef struct fe_complex {
+    double re, im;
+} fe_complex;
+
+typedef enum fe_variant {
+    FE_VARIANT_S = 0, /* a + G: volume terms + ABC; complex symmetric (default) */
+    FE_VARIANT_L = 1, /* a + L + G: the literal Eq. 4 with the penalty surface term; non-symmetric */
+    FE_VARIANT_P = 2  /* (A_L + A_L^T)/2: the paper's symmetrisation by the transpose (Section 3.1.4) */
+} fe_variant;
+
+typedef enum fe_precision {
+    FE_PREC_FP64 = 0,  /* plain method: complex128 matrix, complex128 Krylov loop */
+    FE_PREC_MIXED = 1  /* complex64 Krylov loop inside FP64 iterative refinement */
+} fe_precision;
+
+typedef struct fe_options {
+    void* stream;      /* cudaStream_t for all work of the context; NULL = context-owned stream */
+    int32_t variant;   /* fe_variant; default FE_VARIANT_S */
+    double abc_sigma;  /* weight of the transverse ABC term: -1 dispersion-consistent (default), +1 literal Eq. 3, 0 first order */
+    double penalty_s;  /* grad-div penalty coefficient s (Eq. 2); default 1 */
+} fe_options;
+
+/* Fills *opt with the defaults above. */
+void fe_options_default(fe_options* opt);
+
+typedef struct fe_ctx fe_ctx;
+typedef struct fe_mesh fe_mesh;
+typedef struct fe_system fe_system;
+typedef struct fe_server fe_server;
+
+/* Creates a context on CUDA device `cuda_device`.  opt may be NULL (defaults).
+ * Errors: FE_ERR_INVALID_ARG (out == NULL, bad option), FE_ERR_CUDA. */
+fe_status fe_ctx_create(fe_ctx** out, int cuda_device, const fe_options* opt);
+void fe_ctx_destroy(fe_ctx* ctx);
+/* Blocks until all work queued on the context's stream has finished.
+ * Errors: FE_ERR_INVALID_ARG (NULL), FE_ERR_CUDA (an earlier kernel failed). */
+fe_status fe_ctx_synchronize(fe_ctx* ctx);
+
+/* ------------------------------------------------------------------------
+ * Mesh and block pattern (Section 3.1.2 storage by node rows; Section 4.2.1
+ * structure of the global matrix).  Built on the device by the library's
+ * kernels; the caller's description is copied.
+ * ---------------------------------------------------------------------- */
+typedef struct fe_mesh_desc {
+    int32_t nx, ny, nz;          /* elements per axis, each >= 1 */
+    double h[3];                 /* element edge lengths (m), > 0 */
+    double origin[3];            /* world position of node (0,0,0) (m) */
+    const uint8_t* material;     /* nx*ny*nz bytes indexed by element id; < n_materials or 255 (PEC) */
+    int32_t material_on_device;  /* 0: host pointer; 1: device pointer (read on the context stream) */
+    int32_t n_materials;         /* 1..255 entries in eps_r / mu_r */
+    const fe_complex* eps_r;     /* host, n_materials relative permittivities (eps' - j eps'' for losses) */
+    const fe_complex* mu_r;      /* host, n_materials relative permeabilities */
+} fe_mesh_desc;
+
+typedef struct fe_mesh_stats {
+    int64_t n_elements, n_active_elements;
+    int64_t n_nodes_total, n_nodes; /* all grid nodes / active nodes (block rows) */
+    int64_t n_dof;                  /* 3 * n_nodes */
+    int64_t nnzb;                   /* number of 3x3 blocks */
+    int64_t n_faces_ext, n_faces_pec;
+    int64_t device_bytes;           /* device memory held by the mesh */
+} fe_mesh_stats;
+
+/* Validates the description and builds every integer map on the device.
+ * Errors: FE_ERR_INVALID_ARG (sizes, NULL pointers, material byte outside
+ * the table), FE_ERR_MESH (PEC or non-vacuum material in the outer layer of
+ * elements, i.e. an outer face not in free space), FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_mesh_create(fe_ctx* ctx, const fe_mesh_desc* d, fe_mesh** out);
+fe_status fe_mesh_info(const fe_mesh* m, fe_mesh_stats* out);
+/* Copies the integer maps to caller-allocated HOST buffers; any pointer may
+ * be NULL to skip that map.  Sizes: node_rank[n_nodes_total] (-1 = inactive),
+ * row_ptr[n_nodes + 1], col_idx[nnzb], elem_slot[n_elements*64] (slot of block
+ * (local a, local b) of element e at [64e + 8a + b], -1 for PEC elements),
+ * faces_ext[n_faces_ext], faces_pec[n_faces_pec]. */
+fe_status fe_mesh_export_maps(fe_ctx* ctx, const fe_mesh* m, int32_t* node_rank, int32_t* row_ptr,
+                              int32_t* col_idx, int32_t* elem_slot, int32_t* faces_ext,
+                              int32_t* faces_pec);
+void fe_mesh_destroy(fe_mesh* m);
+
+/* ------------------------------------------------------------------------
+ * Assembly (Section 3.1.2, assembly by degree of freedom: each block row
+ * gathers the contributions of the elements and faces around its node; the
+ * variant's symmetrisation, Section 3.1.4, is applied element by element).
+ * Also builds the 3x3 block-Jacobi inverse (the block form of the diagonal
+ * preconditioning of Section 3.1.5.1) and, for FE_PREC_MIXED, the
+ * round-to-nearest complex64 copies of the matrix and of the inverse.
+ * ---------------------------------------------------------------------- */
+/* Errors: FE_ERR_INVALID_ARG (freq_hz <= 0, bad precision), FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t precision, fe_system** out);
+/* Copies values to caller-allocated HOST buffers (any may be NULL):
+ * vals_c128[nnzb*9*2 doubles], vals_c64[nnzb*9*2 floats] (FE_PREC_MIXED only,
+ * else FE_ERR_INVALID_ARG), dinv_c128[n_nodes*9*2 doubles]. */
+fe_status fe_system_export(fe_ctx* ctx, const fe_system* s, void* vals_c128, void* vals_c64, void* dinv_c128);
+void fe_system_destroy(fe_system* s);
+
+/* ------------------------------------------------------------------------
+ * Right-hand side (Eq. 4): b(W) = G(W, H_i) - int_Sext W.(n x curl H_i) ds
+ * with H_i = p_hat * amplitude * exp(-j k0 k_hat . r).
+ * ---------------------------------------------------------------------- */
+typedef struct fe_planewave {
+    double k_hat[3];      /* unit propagation direction */
+    double p_hat[3];      /* unit H polarisation, orthogonal to k_hat */
+    fe_complex amplitude; /* H0 (A/m) */
+} fe_planewave;
+
+/* b_out: complex128 [n_dof][nrhs]; host buffer, or device when on_device = 1.
+ * Errors: FE_ERR_INVALID_ARG (nrhs < 1, NULL), FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const fe_planewave* waves, void* b_out,
+                 int32_t on_device);
+
+/* y = A x for the block matrix of `s` in `precision` (FE_PREC_FP64: complex128
+ * vectors and matrix; FE_PREC_MIXED: complex64 vectors and the complex64
+ * matrix copy).  x, y: DEVICE buffers [n_dof][nrhs], nrhs >= 1; no aliasing.
+ * This is the sparse product at the heart of the Krylov loop (Section 3.1.5.1). */
+fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y);
+
+/* ------------------------------------------------------------------------
+ * Solve (Sections 3.1.5 and 4.2.5: conjugate gradients on the symmetric
+ * system with diagonal preconditioning; here the complex-symmetric form,
+ * COCG, with 3x3 block-Jacobi preconditioning).  FE_PREC_MIXED runs the
+ * Krylov loop in complex64 inside an FP64 iterative refinement: r = b - A x
+ * in FP64, inner COCG on A_c64 d = r, x += d, until ||b - A x|| / ||b|| <= tol
+ * for every right-hand side.  All right-hand sides are solved together in
+ * one persistent device launch per refinement pass.
+ * ---------------------------------------------------------------------- */
+typedef struct fe_solve_opts {
+    int32_t precision;   /* fe_precision; default FE_PREC_MIXED */
+    double tol;          /* true FP64 relative residual target; default 1e-8 */
+    double inner_tol;    /* relative reduction per inner (complex64) solve; default 1e-4 */
+    int32_t max_iter;    /* cap on total Krylov iterations per right-hand side; default 20000 */
+    int32_t max_outer;   /* cap on refinement passes; default 30 */
+    int32_t rhs_tile;    /* right-hand sides per device pass, 0 = automatic */
+} fe_solve_opts;
+
+void fe_solve_opts_default(fe_solve_opts* o);
+
+typedef struct fe_solve_report {
+    int32_t status;        /* fe_status of this right-hand side */
+    int32_t iterations;    /* Krylov iterations (sum over refinement passes) */
+    int32_t outer;         /* refinement passes (true-residual evaluations - 1) */
+    int32_t reserved;
+    double rel_residual;   /* final true FP64 ||b - A x|| / ||b|| */
+} fe_solve_report;
+
+/* Builds B from the plane waves (Eq. 4) and solves A X = B.
+ * x_out: complex128 [n_dof][nrhs], host or device (x_on_device).  rep:
+ * optional host array of nrhs reports.  Returns FE_OK when every column met
+ * tol, else the first failing column's status (the reports and x are still
+ * written).  Errors: FE_ERR_INVALID_ARG, FE_ERR_OOM, FE_ERR_CUDA,
+ * FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN, FE_ERR_TIMEOUT. */
+fe_status fe_solve_batch(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const fe_planewave* waves,
+                         const fe_solve_opts* o, void* x_out, int32_t x_on_device, fe_solve_report* rep);
+
+/* As fe_solve_batch with a caller right-hand side b (complex128 [n_dof][nrhs],
+ * host or device as b_on_device) and optional initial guess in x_out
+ * (use_x0 = 1: x_out holds x0 on entry; this is how a solve is resumed). */
+fe_status fe_solve_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b, int32_t b_on_device,
+                       const fe_solve_opts* o, void* x_out, int32_t x_on_device, int32_t use_x0,
+                       fe_solve_report* rep);
+
+/* Device-side statistics of the most recent fe_solve_batch / fe_solve_rhs
+ * call on this context, measured with CUDA events on the context stream
+ * around the persistent solve launches. */
+typedef struct fe_solve_stats {
+    double kernel_ms;        /* device time of the persistent solve launch(es), summed over tiles */
+    int64_t launches;        /* persistent launches (one per right-hand-side tile) */
+    int64_t inner_iters;     /* Krylov iterations, summed over right-hand sides */
+    int64_t passes;          /* refinement passes (true-residual evaluations), summed over tiles */
+    int64_t tile_width;      /* right-hand sides per launch */
+    int64_t grid_ctas;       /* CTAs of the cooperative launch */
+} fe_solve_stats;
+fe_status fe_last_solve_stats(const fe_ctx* ctx, fe_solve_stats* out);
+
+/* Thread-local description of the last error of the calling thread. */
+const char* fe_last_error(void);
+/* Number of kernel launches the library has issued on any context so far. */
+int64_t fe_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FE_H */

@@ -1,0 +1,379 @@
+// Assembly of Eq. 4's left-hand side into 3x3-block rows.
+//
+// Element matrices (Eq. 1 with the Eq. 2 volume penalty) of an axis-aligned
+// brick are sums of Kronecker products of three 1-D matrices,
+//     M1 = h/6 [[2,1],[1,2]],  K1 = 1/h [[1,-1],[-1,1]],
+//     D1[p][q] = int phi_p' phi_q = (p == 0 ? -1/2 : +1/2),
+// so every entry has a closed form.  Per material one 24x24 table is built
+// (k_tables), plus per face orientation the absorbing-boundary form G of
+// Eq. 3 and the penalty surface term of Eq. 4.  The assembly kernel then
+// follows the paper's assembly by degree of freedom (Section 3.1.2): one warp
+// per node gathers, for each of the node's up to 27 blocks, the contributions
+// of the elements and faces shared with the neighbour, with no atomics.  The
+// symmetrisation by the transpose (Section 3.1.4, variant P) is applied to
+// each face table, since (sum_e A_e)^T = sum_e A_e^T.  The same warp inverts
+// the diagonal block for the block-Jacobi preconditioner.
+#include "fe_internal.cuh"
+
+#include <new>
+
+namespace fe {
+
+struct Cx {
+    double re, im;
+};
+__device__ __forceinline__ Cx cx(double r, double i) { return Cx{r, i}; }
+__device__ __forceinline__ Cx operator+(Cx a, Cx b) { return Cx{a.re + b.re, a.im + b.im}; }
+__device__ __forceinline__ Cx operator-(Cx a, Cx b) { return Cx{a.re - b.re, a.im - b.im}; }
+__device__ __forceinline__ Cx operator*(Cx a, Cx b) {
+    return Cx{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+__device__ __forceinline__ Cx operator*(double s, Cx a) { return Cx{s * a.re, s * a.im}; }
+__device__ __forceinline__ Cx cdiv(Cx a, Cx b) {
+    const double d = b.re * b.re + b.im * b.im;
+    return Cx{(a.re * b.re + a.im * b.im) / d, (a.im * b.re - a.re * b.im) / d};
+}
+
+struct TableParams {
+    double h[3];
+    double k0, sigma, s_pen;
+    int variant;
+    int n_mat;
+    Cx eps[64], mu[64];
+};
+
+__device__ __forceinline__ double m1(double h, int p, int q) { return h * (p == q ? 2.0 : 1.0) / 6.0; }
+__device__ __forceinline__ double k1(double h, int p, int q) { return (p == q ? 1.0 : -1.0) / h; }
+__device__ __forceinline__ double d1(int p) { return p == 0 ? -0.5 : 0.5; }
+
+// int d_g N_a d_d N_b over the brick (a, b local node indices 0..7).
+__device__ double cterm(const double* h, int g, int d, int a, int b) {
+    const int ac[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+    const int bc[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+    if (g == d) {
+        double v = k1(h[g], ac[g], bc[g]);
+        for (int t = 0; t < 3; ++t)
+            if (t != g) v *= m1(h[t], ac[t], bc[t]);
+        return v;
+    }
+    const int t = 3 - g - d;
+    return d1(ac[g]) * d1(bc[d]) * m1(h[t], ac[t], bc[t]);
+}
+
+__device__ double mterm(const double* h, int a, int b) {
+    return m1(h[0], a & 1, b & 1) * m1(h[1], (a >> 1) & 1, (b >> 1) & 1) * m1(h[2], (a >> 2) & 1, (b >> 2) & 1);
+}
+
+// Volume entry (a, al; b, be) of Eq. 1 + Eq. 2:
+//   (1/eps)(delta_ab G_ab - C^{be,al}_ab) + s C^{al,be}_ab - k0^2 mu delta M_ab
+__device__ Cx vol_entry(const TableParams& P, Cx inv_eps, Cx mu, int a, int al, int b, int be) {
+    double cc = -cterm(P.h, be, al, a, b);
+    if (al == be) cc += cterm(P.h, 0, 0, a, b) + cterm(P.h, 1, 1, a, b) + cterm(P.h, 2, 2, a, b);
+    const double dd = P.s_pen * cterm(P.h, al, be, a, b);
+    Cx v = cc * inv_eps + cx(dd, 0.0);
+    if (al == be) v = v - (P.k0 * P.k0 * mterm(P.h, a, b)) * mu;
+    return v;
+}
+
+// Absorbing boundary form of Eq. 3 on face f (weak form, transverse
+// Laplacian integrated by parts):  j k0 int W_t.H_t + sigma j/(2k0) int
+// grad_t W_t : grad_t H_t, only tangential components, only face nodes.
+__device__ Cx abc_entry(const TableParams& P, int f, int a, int al, int b, int be) {
+    const int nu = f >> 1, side = f & 1;
+    const int ac[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+    const int bc[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+    if (al != be || al == nu || ac[nu] != side || bc[nu] != side) return cx(0, 0);
+    const int t1 = nu == 0 ? 1 : 0, t2 = nu == 2 ? 1 : 2;
+    const double m_1 = m1(P.h[t1], ac[t1], bc[t1]), m_2 = m1(P.h[t2], ac[t2], bc[t2]);
+    const double mf = m_1 * m_2;
+    const double kf = k1(P.h[t1], ac[t1], bc[t1]) * m_2 + m_1 * k1(P.h[t2], ac[t2], bc[t2]);
+    return cx(0.0, P.k0 * mf + P.sigma * kf / (2.0 * P.k0));
+}
+
+// Penalty surface term of Eq. 4 on face f: -s n_al int N_a d_be N_b ds.
+__device__ double pen_entry(const TableParams& P, int f, int a, int al, int b, int be) {
+    const int nu = f >> 1, side = f & 1;
+    const int ac[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+    const int bc[3] = {b & 1, (b >> 1) & 1, (b >> 2) & 1};
+    if (al != nu || ac[nu] != side) return 0.0;
+    double v = (be == nu) ? (bc[nu] == 1 ? 1.0 : -1.0) / P.h[nu] : (bc[nu] == side ? 1.0 : 0.0);
+    for (int t = 0; t < 3; ++t) {
+        if (t == nu) continue;
+        v *= (be == t) ? d1(bc[t]) : m1(P.h[t], ac[t], bc[t]);
+    }
+    return -P.s_pen * (side ? 1.0 : -1.0) * v;
+}
+
+// Tables, block-major: table[(a*8 + b)*9 + al*3 + be].  Table t < n_mat is
+// the volume matrix of material t; n_mat + f is the outer-face table of
+// orientation f; n_mat + 6 + f the PEC-face table.
+__global__ void k_tables(TableParams P, double2* __restrict__ tab) {
+    const int t = blockIdx.x;
+    const int idx = threadIdx.x;  // 0..575, block-major
+    const int blk = idx / 9, w = idx % 9;
+    const int a = blk >> 3, b = blk & 7, al = w / 3, be = w % 3;
+    Cx v = cx(0, 0);
+    if (t < P.n_mat) {
+        v = vol_entry(P, cdiv(cx(1, 0), P.eps[t]), P.mu[t], a, al, b, be);
+    } else {
+        const int f = (t - P.n_mat) % 6;
+        const bool ext = (t - P.n_mat) < 6;
+        double pen = 0.0;
+        if (P.variant == FE_VARIANT_L) {
+            pen = pen_entry(P, f, a, al, b, be);
+        } else if (P.variant == FE_VARIANT_P) {
+            pen = 0.5 * (pen_entry(P, f, a, al, b, be) + pen_entry(P, f, b, be, a, al));
+        }
+        v = cx(pen, 0.0);
+        if (ext) v = v + abc_entry(P, f, a, al, b, be);
+    }
+    tab[(size_t)t * 576 + idx] = make_double2(v.re, v.im);
+}
+
+// One warp per block row; lane l < 27 owns the block at neighbour offset
+// (l % 3 - 1, (l / 3) % 3 - 1, l / 9 - 1).
+__global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ mat, int nx, int ny, int nz,
+                                                  int n_mat, const int* __restrict__ node_id,
+                                                  const int* __restrict__ row_ptr,
+                                                  const double2* __restrict__ tab, double2* __restrict__ val64,
+                                                  float2* __restrict__ val32, double2* __restrict__ dinv64,
+                                                  float2* __restrict__ dinv32, int n_act, int* __restrict__ status) {
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (warp >= n_act) return;
+    const int id = node_id[warp];
+    const int i = id % (nx + 1), j = (id / (nx + 1)) % (ny + 1), k = id / ((nx + 1) * (ny + 1));
+    // elements around the node (bit ex + 2ey + 4ez: element (i-1+ex, j-1+ey, k-1+ez))
+    unsigned emask = 0;
+    if (lane < 8) {
+        const int ex = lane & 1, ey = (lane >> 1) & 1, ez = (lane >> 2) & 1;
+        const int a = i - 1 + ex, b = j - 1 + ey, c = k - 1 + ez;
+        if (a >= 0 && a < nx && b >= 0 && b < ny && c >= 0 && c < nz &&
+            mat[a + (int64_t)nx * (b + (int64_t)ny * c)] != kPEC)
+            emask = 1;
+    }
+    emask = __ballot_sync(0xffffffffu, emask) & 0xFFu;
+    const int dx = lane % 3 - 1, dy = (lane / 3) % 3 - 1, dz = lane / 9 - 1;
+    const unsigned ax = dx < 0 ? 0x55u : dx > 0 ? 0xAAu : 0xFFu;
+    const unsigned ay = dy < 0 ? 0x33u : dy > 0 ? 0xCCu : 0xFFu;
+    const unsigned az = dz < 0 ? 0x0Fu : dz > 0 ? 0xF0u : 0xFFu;
+    const unsigned shared = lane < 27 ? (emask & ax & ay & az) : 0u;
+    const unsigned exists = __ballot_sync(0xffffffffu, shared != 0);
+    if (!shared) return;
+    const int slot = row_ptr[warp] + __popc(exists & ((1u << lane) - 1u));
+
+    double2 acc[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) acc[q] = make_double2(0.0, 0.0);
+    unsigned sm = shared;
+    while (sm) {
+        const int p = __ffs(sm) - 1;
+        sm &= sm - 1;
+        const int ex = p & 1, ey = (p >> 1) & 1, ez = (p >> 2) & 1;
+        const int ei = i - 1 + ex, ej = j - 1 + ey, ek = k - 1 + ez;
+        // local indices of the row node (a) and the neighbour (b) in this element
+        const int a = (1 - ex) + 2 * (1 - ey) + 4 * (1 - ez);
+        const int b = (1 - ex + dx) + 2 * (1 - ey + dy) + 4 * (1 - ez + dz);
+        const int64_t e = ei + (int64_t)nx * (ej + (int64_t)ny * ek);
+        const int m = mat[e];
+        const double2* tv = tab + (size_t)m * 576 + (a * 8 + b) * 9;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const double2 v = __ldg(tv + q);
+            acc[q].x += v.x;
+            acc[q].y += v.y;
+        }
+        // faces of this element on the outer box or against a PEC element
+        const int ec[3] = {ei, ej, ek};
+        const int dim[3] = {nx, ny, nz};
+#pragma unroll
+        for (int f = 0; f < 6; ++f) {
+            const int axis = f >> 1, side = f & 1;
+            const bool on_box = side ? ec[axis] == dim[axis] - 1 : ec[axis] == 0;
+            int tsel = -1;
+            if (on_box) {
+                tsel = n_mat + f;
+            } else {
+                int nb[3] = {ei, ej, ek};
+                nb[axis] += side ? 1 : -1;
+                if (mat[nb[0] + (int64_t)nx * (nb[1] + (int64_t)ny * nb[2])] == kPEC) tsel = n_mat + 6 + f;
+            }
+            if (tsel >= 0) {
+                const double2* fv = tab + (size_t)tsel * 576 + (a * 8 + b) * 9;
+#pragma unroll
+                for (int q = 0; q < 9; ++q) {
+                    const double2 v = __ldg(fv + q);
+                    acc[q].x += v.x;
+                    acc[q].y += v.y;
+                }
+            }
+        }
+    }
+    double2* o64 = val64 + (size_t)slot * 9;
+#pragma unroll
+    for (int q = 0; q < 9; ++q) o64[q] = acc[q];
+    if (val32) {
+        float2* o32 = val32 + (size_t)slot * 9;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) o32[q] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
+    }
+    if (lane == 13) {  // diagonal block: 3x3 complex inverse by cofactors
+        Cx A[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) A[r][c] = cx(acc[3 * r + c].x, acc[3 * r + c].y);
+        Cx C[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                C[r][c] = A[(r + 1) % 3][(c + 1) % 3] * A[(r + 2) % 3][(c + 2) % 3] -
+                          A[(r + 1) % 3][(c + 2) % 3] * A[(r + 2) % 3][(c + 1) % 3];
+        const Cx det = A[0][0] * C[0][0] + A[0][1] * C[0][1] + A[0][2] * C[0][2];
+        if (det.re == 0.0 && det.im == 0.0) {
+            atomicOr(status, kDevSingular);
+            return;
+        }
+        const Cx inv_det = cdiv(cx(1, 0), det);
+        double2* d64 = dinv64 + (size_t)warp * 9;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const Cx v = C[c][r] * inv_det;  // inverse = adjugate / det, adjugate = cofactor^T
+                d64[3 * r + c] = make_double2(v.re, v.im);
+                if (dinv32)
+                    dinv32[(size_t)warp * 9 + 3 * r + c] =
+                        make_float2(__double2float_rn(v.re), __double2float_rn(v.im));
+            }
+    }
+}
+
+static void system_free(fe_system* s) {
+    cudaStream_t st = s->ctx->stream;
+    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->dinv64, &s->dinv32}) dev_free(st, *b);
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t precision, fe_system** out) {
+    if (!ctx || !m || !out) {
+        set_error("fe_assemble: NULL argument");
+        return FE_ERR_INVALID_ARG;
+    }
+    *out = nullptr;
+    if (!(freq_hz > 0.0) || (precision != FE_PREC_FP64 && precision != FE_PREC_MIXED)) {
+        set_error("fe_assemble: frequency must be > 0 and precision FP64 or MIXED");
+        return FE_ERR_INVALID_ARG;
+    }
+    if (m->n_mat > 64) {
+        set_error("fe_assemble: at most 64 materials are supported");
+        return FE_ERR_UNSUPPORTED;
+    }
+    cudaSetDevice(ctx->device);
+    fe_system* s = new (std::nothrow) fe_system();
+    if (!s) {
+        set_error("fe_assemble: host allocation failed");
+        return FE_ERR_OOM;
+    }
+    s->ctx = ctx;
+    s->mesh = m;
+    s->freq = freq_hz;
+    s->k0 = 2.0 * kPi * freq_hz / kC0;
+    s->precision = precision;
+    s->variant = ctx->opt.variant;
+    s->sigma = ctx->opt.abc_sigma;
+    s->s_pen = ctx->opt.penalty_s;
+    cudaStream_t st = ctx->stream;
+    auto fail = [&](fe_status e) {
+        system_free(s);
+        delete s;
+        return e;
+    };
+    fe_status e;
+    const int n_tab = m->n_mat + 12;
+    if ((e = dev_alloc(st, s->tables, (size_t)n_tab * 576 * sizeof(double2))) != FE_OK) return fail(e);
+    if ((e = dev_alloc(st, s->val64, (size_t)m->nnzb * 9 * sizeof(double2))) != FE_OK) return fail(e);
+    if ((e = dev_alloc(st, s->dinv64, (size_t)m->n_act * 9 * sizeof(double2))) != FE_OK) return fail(e);
+    if (precision == FE_PREC_MIXED) {
+        if ((e = dev_alloc(st, s->val32, (size_t)m->nnzb * 9 * sizeof(float2))) != FE_OK) return fail(e);
+        if ((e = dev_alloc(st, s->dinv32, (size_t)m->n_act * 9 * sizeof(float2))) != FE_OK) return fail(e);
+    }
+    TableParams P{};
+    for (int a = 0; a < 3; ++a) P.h[a] = m->h[a];
+    P.k0 = s->k0;
+    P.sigma = s->sigma;
+    P.s_pen = s->s_pen;
+    P.variant = s->variant;
+    P.n_mat = m->n_mat;
+    for (int q = 0; q < m->n_mat; ++q) {
+        P.eps[q] = Cx{m->eps[q].re, m->eps[q].im};
+        P.mu[q] = Cx{m->mu[q].re, m->mu[q].im};
+    }
+    int* d_status = (int*)ctx->small.ptr + 8;
+    cudaMemsetAsync(d_status, 0, sizeof(int), st);
+    k_tables<<<n_tab, 576, 0, st>>>(P, (double2*)s->tables.ptr);
+    {
+        count_launches(1);
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) {
+            set_error("k_tables launch: %s", cudaGetErrorString(ce));
+            return fail(FE_ERR_CUDA);
+        }
+    }
+    const int threads = 256;
+    const unsigned blocks = (unsigned)(((int64_t)m->n_act * 32 + threads - 1) / threads);
+    k_assemble<<<blocks, threads, 0, st>>>((const uint8_t*)m->material.ptr, m->nx, m->ny, m->nz, m->n_mat,
+                                           (const int*)m->node_id.ptr, (const int*)m->row_ptr.ptr,
+                                           (const double2*)s->tables.ptr, (double2*)s->val64.ptr,
+                                           (float2*)s->val32.ptr, (double2*)s->dinv64.ptr, (float2*)s->dinv32.ptr,
+                                           m->n_act, d_status);
+    {
+        count_launches(1);
+        cudaError_t ce = cudaGetLastError();
+        if (ce != cudaSuccess) {
+            set_error("k_assemble launch: %s", cudaGetErrorString(ce));
+            return fail(FE_ERR_CUDA);
+        }
+    }
+    *out = s;
+    return FE_OK;
+}
+
+fe_status fe_system_export(fe_ctx* ctx, const fe_system* s, void* vals_c128, void* vals_c64, void* dinv_c128) {
+    if (!ctx || !s) {
+        set_error("fe_system_export: NULL argument");
+        return FE_ERR_INVALID_ARG;
+    }
+    if (vals_c64 && !s->val32.ptr) {
+        set_error("fe_system_export: no complex64 copy (system assembled in FP64)");
+        return FE_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = ctx->stream;
+    const fe_mesh* m = s->mesh;
+    if (vals_c128)
+        FE_CUDA(cudaMemcpyAsync(vals_c128, s->val64.ptr, (size_t)m->nnzb * 9 * sizeof(double2),
+                                cudaMemcpyDeviceToHost, st));
+    if (vals_c64)
+        FE_CUDA(cudaMemcpyAsync(vals_c64, s->val32.ptr, (size_t)m->nnzb * 9 * sizeof(float2),
+                                cudaMemcpyDeviceToHost, st));
+    if (dinv_c128)
+        FE_CUDA(cudaMemcpyAsync(dinv_c128, s->dinv64.ptr, (size_t)m->n_act * 9 * sizeof(double2),
+                                cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    return FE_OK;
+}
+
+void fe_system_destroy(fe_system* s) {
+    if (!s) return;
+    cudaSetDevice(s->ctx->device);
+    system_free(s);
+    delete s;
+}
+
+}  // extern "C"

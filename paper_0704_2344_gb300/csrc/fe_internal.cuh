@@ -1,0 +1,100 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstdint>
+#include <cstdio>
+#include <vector>
+
+#include "../../include/fe.h"
+
+namespace fe {
+
+constexpr uint8_t kPEC = 255;
+constexpr double kC0 = 299792458.0;
+constexpr double kPi = 3.14159265358979323846;
+
+// Device-side error codes written to the context's status word.
+enum : int { kDevOk = 0, kDevTimeout = 1, kDevBadIndex = 2, kDevSingular = 4 };
+
+void set_error(const char* fmt, ...);
+void count_launches(int64_t n);
+
+#define FE_CUDA(call)                                                                      \
+    do {                                                                                   \
+        cudaError_t e_ = (call);                                                           \
+        if (e_ != cudaSuccess) {                                                           \
+            ::fe::set_error("%s:%d %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_)); \
+            return e_ == cudaErrorMemoryAllocation ? FE_ERR_OOM : FE_ERR_CUDA;             \
+        }                                                                                  \
+    } while (0)
+
+#define FE_LAUNCHED()                                                                      \
+    do {                                                                                   \
+        ::fe::count_launches(1);                                                           \
+        cudaError_t e_ = cudaGetLastError();                                               \
+        if (e_ != cudaSuccess) {                                                           \
+            ::fe::set_error("%s:%d launch: %s", __FILE__, __LINE__, cudaGetErrorString(e_)); \
+            return FE_ERR_CUDA;                                                            \
+        }                                                                                  \
+    } while (0)
+
+#define FE_TRY(expr)                  \
+    do {                              \
+        fe_status s_ = (expr);        \
+        if (s_ != FE_OK) return s_;   \
+    } while (0)
+
+// Stream-ordered device buffer owned by the library.
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+fe_status dev_alloc(cudaStream_t st, DevBuf& b, size_t bytes);
+void dev_free(cudaStream_t st, DevBuf& b);
+
+// Exclusive prefix sum of n int32 values (in may alias out); writes the total
+// to *d_total (device).  Uses `tmp` (grown as needed) for block sums.
+fe_status scan_exclusive(cudaStream_t st, const int* in, int* out, int64_t n, int* d_total, DevBuf& tmp);
+
+}  // namespace fe
+
+struct fe_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    fe_options opt{};
+    int num_sms = 0;
+    fe::DevBuf scan_tmp;
+    fe::DevBuf small;  // small device scratch: totals, status words
+    int* h_small = nullptr;  // pinned host mirror of `small` (64 ints)
+    fe_solve_stats last_solve{};
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+struct fe_mesh {
+    fe_ctx* ctx = nullptr;
+    int nx = 0, ny = 0, nz = 0;
+    double h[3]{}, origin[3]{};
+    int64_t n_el = 0, n_nodes_total = 0;
+    int n_act = 0, nnzb = 0, n_ext = 0, n_pec = 0, n_act_el = 0;
+    int n_mat = 0;
+    std::vector<fe_complex> eps, mu;
+    fe::DevBuf material, node_rank, node_id, row_ptr, col_idx, elem_slot, faces_ext, faces_pec;
+    int64_t bytes = 0;
+};
+
+struct fe_system {
+    fe_ctx* ctx = nullptr;
+    const fe_mesh* mesh = nullptr;
+    double freq = 0, k0 = 0;
+    int precision = FE_PREC_MIXED;
+    int variant = FE_VARIANT_S;
+    double sigma = -1, s_pen = 1;
+    fe::DevBuf tables;               // double2 [(n_mat + 12) * 576], block-major
+    fe::DevBuf val64, val32;         // double2 / float2 [nnzb * 9]
+    fe::DevBuf dinv64, dinv32;       // double2 / float2 [n_act * 9]
+};

@@ -1,0 +1,340 @@
+"""Python binding of the C ABI in include/fe.h (ctypes, argument marshalling
+only).  Every function keeps the C name; handles are opaque ctypes pointers;
+errors raise FeError carrying the fe_status and fe_last_error().  Device
+buffers are passed as integer addresses (e.g. torch.Tensor.data_ptr()).
+
+The library must have been built (paper_0704_2344_gb300.build.build()); a
+missing library raises instead of falling back to anything else."""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+
+import numpy as np
+
+FE_OK = 0
+FE_PENDING = 1
+FE_ERR_INVALID_ARG = -1
+FE_ERR_MESH = -2
+FE_ERR_OOM = -3
+FE_ERR_BREAKDOWN = -4
+FE_ERR_NOT_CONVERGED = -5
+FE_ERR_TIMEOUT = -6
+FE_ERR_CUDA = -7
+FE_ERR_UNSUPPORTED = -8
+
+FE_VARIANT_S, FE_VARIANT_L, FE_VARIANT_P = 0, 1, 2
+FE_PREC_FP64, FE_PREC_MIXED = 0, 1
+
+LIB_PATH = Path(__file__).resolve().parent / "libfe_gb300.so"
+
+
+class FeError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where} -> status {status}: {msg}")
+        self.status = status
+
+
+class fe_complex(C.Structure):
+    _fields_ = [("re", C.c_double), ("im", C.c_double)]
+
+
+class fe_options(C.Structure):
+    _fields_ = [("stream", C.c_void_p), ("variant", C.c_int32), ("abc_sigma", C.c_double),
+                ("penalty_s", C.c_double)]
+
+
+class fe_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double * 3),
+                ("origin", C.c_double * 3), ("material", C.c_void_p), ("material_on_device", C.c_int32),
+                ("n_materials", C.c_int32), ("eps_r", C.POINTER(fe_complex)), ("mu_r", C.POINTER(fe_complex))]
+
+
+class fe_mesh_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("n_elements", "n_active_elements", "n_nodes_total", "n_nodes",
+                                          "n_dof", "nnzb", "n_faces_ext", "n_faces_pec", "device_bytes")]
+
+
+class fe_planewave(C.Structure):
+    _fields_ = [("k_hat", C.c_double * 3), ("p_hat", C.c_double * 3), ("amplitude", fe_complex)]
+
+
+class fe_solve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
+                ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32)]
+
+
+class fe_solve_stats(C.Structure):
+    _fields_ = [("kernel_ms", C.c_double), ("launches", C.c_int64), ("inner_iters", C.c_int64),
+                ("passes", C.c_int64), ("tile_width", C.c_int64), ("grid_ctas", C.c_int64)]
+
+
+class fe_solve_report(C.Structure):
+    _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("outer", C.c_int32),
+                ("reserved", C.c_int32), ("rel_residual", C.c_double)]
+
+
+_lib = None
+P = C.c_void_p
+
+
+def load() -> C.CDLL:
+    """Loads libfe_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not LIB_PATH.exists():
+        raise FileNotFoundError(f"{LIB_PATH} is missing: build it with paper_0704_2344_gb300.build.build()")
+    lib = C.CDLL(str(LIB_PATH))
+    sig = {
+        "fe_options_default": (None, [C.POINTER(fe_options)]),
+        "fe_ctx_create": (C.c_int, [C.POINTER(P), C.c_int, C.POINTER(fe_options)]),
+        "fe_ctx_destroy": (None, [P]),
+        "fe_ctx_synchronize": (C.c_int, [P]),
+        "fe_mesh_create": (C.c_int, [P, C.POINTER(fe_mesh_desc), C.POINTER(P)]),
+        "fe_mesh_info": (C.c_int, [P, C.POINTER(fe_mesh_stats)]),
+        "fe_mesh_export_maps": (C.c_int, [P, P, P, P, P, P, P, P]),
+        "fe_mesh_destroy": (None, [P]),
+        "fe_assemble": (C.c_int, [P, P, C.c_double, C.c_int32, C.POINTER(P)]),
+        "fe_system_export": (C.c_int, [P, P, P, P, P]),
+        "fe_system_destroy": (None, [P]),
+        "fe_rhs": (C.c_int, [P, P, C.c_int32, C.POINTER(fe_planewave), P, C.c_int32]),
+        "fe_spmv": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P]),
+        "fe_solve_opts_default": (None, [C.POINTER(fe_solve_opts)]),
+        "fe_solve_batch": (C.c_int, [P, P, C.c_int32, C.POINTER(fe_planewave), C.POINTER(fe_solve_opts), P,
+                                     C.c_int32, C.POINTER(fe_solve_report)]),
+        "fe_solve_rhs": (C.c_int, [P, P, C.c_int32, P, C.c_int32, C.POINTER(fe_solve_opts), P, C.c_int32,
+                                   C.c_int32, C.POINTER(fe_solve_report)]),
+        "fe_last_solve_stats": (C.c_int, [P, C.POINTER(fe_solve_stats)]),
+        "fe_last_error": (C.c_char_p, []),
+        "fe_launch_count": (C.c_int64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in dir(load()) if n.startswith("fe_")]
+
+
+def _check(status: int, where: str, ok=(FE_OK,)):
+    if status not in ok:
+        raise FeError(status, where, load().fe_last_error().decode(errors="replace"))
+    return status
+
+
+def fe_last_error() -> str:
+    return load().fe_last_error().decode(errors="replace")
+
+
+def fe_launch_count() -> int:
+    return int(load().fe_launch_count())
+
+
+def fe_last_solve_stats(ctx) -> dict:
+    s = fe_solve_stats()
+    _check(load().fe_last_solve_stats(ctx, C.byref(s)), "fe_last_solve_stats")
+    return {n: (float(getattr(s, n)) if n == "kernel_ms" else int(getattr(s, n))) for n, _ in fe_solve_stats._fields_}
+
+
+def _ptr(a) -> int:
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+# --------------------------------------------------------------------------
+def fe_ctx_create(device: int = 0, stream: int | None = None, variant: int = FE_VARIANT_S,
+                  abc_sigma: float = -1.0, penalty_s: float = 1.0):
+    lib = load()
+    opt = fe_options()
+    lib.fe_options_default(C.byref(opt))
+    opt.stream = stream
+    opt.variant = variant
+    opt.abc_sigma = abc_sigma
+    opt.penalty_s = penalty_s
+    out = P()
+    _check(lib.fe_ctx_create(C.byref(out), device, C.byref(opt)), "fe_ctx_create")
+    return out
+
+
+def fe_ctx_destroy(ctx):
+    load().fe_ctx_destroy(ctx)
+
+
+def fe_ctx_synchronize(ctx):
+    _check(load().fe_ctx_synchronize(ctx), "fe_ctx_synchronize")
+
+
+def fe_mesh_create(ctx, nx, ny, nz, h, origin, material, eps_r, mu_r, material_on_device=False):
+    """material: numpy uint8 array (nz, ny, nx) or a device address of nx*ny*nz bytes."""
+    lib = load()
+    d = fe_mesh_desc()
+    d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
+    d.h = (C.c_double * 3)(*[float(v) for v in h])
+    d.origin = (C.c_double * 3)(*[float(v) for v in origin])
+    keep = None
+    if material_on_device:
+        d.material = int(material)
+        d.material_on_device = 1
+    else:
+        keep = np.ascontiguousarray(material, dtype=np.uint8)
+        if keep.size != d.nx * d.ny * d.nz:
+            raise ValueError("material size does not match the grid")
+        d.material = keep.ctypes.data
+        d.material_on_device = 0
+    eps = np.ascontiguousarray(np.asarray(eps_r, dtype=np.complex128))
+    mu = np.ascontiguousarray(np.asarray(mu_r, dtype=np.complex128))
+    if eps.shape != mu.shape:
+        raise ValueError("eps_r and mu_r differ in length")
+    d.n_materials = eps.size
+    d.eps_r = eps.ctypes.data_as(C.POINTER(fe_complex))
+    d.mu_r = mu.ctypes.data_as(C.POINTER(fe_complex))
+    out = P()
+    _check(lib.fe_mesh_create(ctx, C.byref(d), C.byref(out)), "fe_mesh_create")
+    del keep
+    return out
+
+
+def fe_mesh_create_from(ctx, problem, material_device_ptr: int | None = None):
+    """Marshals a workloads.VoxelProblem (or any object with the same fields)."""
+    mat = problem.material if material_device_ptr is None else material_device_ptr
+    return fe_mesh_create(ctx, problem.nx, problem.ny, problem.nz, problem.h, problem.origin, mat,
+                          problem.eps_r, problem.mu_r, material_on_device=material_device_ptr is not None)
+
+
+def fe_mesh_info(mesh) -> dict:
+    s = fe_mesh_stats()
+    _check(load().fe_mesh_info(mesh, C.byref(s)), "fe_mesh_info")
+    return {n: int(getattr(s, n)) for n, _ in fe_mesh_stats._fields_}
+
+
+def fe_mesh_export_maps(ctx, mesh) -> dict:
+    info = fe_mesh_info(mesh)
+    out = {
+        "node_rank": np.empty(info["n_nodes_total"], np.int32),
+        "row_ptr": np.empty(info["n_nodes"] + 1, np.int32),
+        "col_idx": np.empty(info["nnzb"], np.int32),
+        "elem_slot": np.empty(info["n_elements"] * 64, np.int32),
+        "faces_ext": np.empty(info["n_faces_ext"], np.int32),
+        "faces_pec": np.empty(info["n_faces_pec"], np.int32),
+    }
+    _check(load().fe_mesh_export_maps(ctx, mesh, *[out[k].ctypes.data for k in
+                                                    ("node_rank", "row_ptr", "col_idx", "elem_slot",
+                                                     "faces_ext", "faces_pec")]), "fe_mesh_export_maps")
+    out["elem_slot"] = out["elem_slot"].reshape(-1, 8, 8)
+    return out
+
+
+def fe_mesh_destroy(mesh):
+    load().fe_mesh_destroy(mesh)
+
+
+def fe_assemble(ctx, mesh, freq_hz: float, precision: int = FE_PREC_MIXED):
+    out = P()
+    _check(load().fe_assemble(ctx, mesh, float(freq_hz), int(precision), C.byref(out)), "fe_assemble")
+    return out
+
+
+def fe_system_export(ctx, system, mesh, c128=True, c64=False, dinv=False) -> dict:
+    info = fe_mesh_info(mesh)
+    out = {}
+    a = np.empty((info["nnzb"], 3, 3), np.complex128) if c128 else None
+    b = np.empty((info["nnzb"], 3, 3), np.complex64) if c64 else None
+    d = np.empty((info["n_nodes"], 3, 3), np.complex128) if dinv else None
+    _check(load().fe_system_export(ctx, system, _ptr(a), _ptr(b), _ptr(d)), "fe_system_export")
+    if c128:
+        out["c128"] = a
+    if c64:
+        out["c64"] = b
+    if dinv:
+        out["dinv"] = d
+    return out
+
+
+def fe_system_destroy(system):
+    load().fe_system_destroy(system)
+
+
+def planewave_array(waves) -> C.Array:
+    """waves: workloads.PlaneWaves (k_hat [R,3], p_hat [R,3], amplitude [R])."""
+    R = waves.k_hat.shape[0]
+    arr = (fe_planewave * R)()
+    for r in range(R):
+        arr[r].k_hat = (C.c_double * 3)(*waves.k_hat[r])
+        arr[r].p_hat = (C.c_double * 3)(*waves.p_hat[r])
+        arr[r].amplitude = fe_complex(float(np.real(waves.amplitude[r])), float(np.imag(waves.amplitude[r])))
+    return arr
+
+
+def fe_rhs(ctx, system, waves, n_dof: int, out=None, on_device: bool = False):
+    """Returns B [n_dof, R] complex128 (host) unless `out` is a device address."""
+    arr = planewave_array(waves)
+    R = len(arr)
+    if out is None:
+        host = np.empty((n_dof, R), np.complex128)
+        _check(load().fe_rhs(ctx, system, R, arr, host.ctypes.data, 0), "fe_rhs")
+        return host
+    _check(load().fe_rhs(ctx, system, R, arr, _ptr(out), 1 if on_device else 0), "fe_rhs")
+    return out
+
+
+def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
+    _check(load().fe_spmv(ctx, system, int(precision), int(nrhs), _ptr(x), _ptr(y)), "fe_spmv")
+
+
+def solve_opts(precision=FE_PREC_MIXED, tol=1e-8, inner_tol=1e-4, max_iter=20000, max_outer=30,
+               rhs_tile=0) -> fe_solve_opts:
+    o = fe_solve_opts()
+    load().fe_solve_opts_default(C.byref(o))
+    o.precision, o.tol, o.inner_tol = int(precision), float(tol), float(inner_tol)
+    o.max_iter, o.max_outer, o.rhs_tile = int(max_iter), int(max_outer), int(rhs_tile)
+    return o
+
+
+def _reports(rep) -> list[dict]:
+    return [{"status": r.status, "iterations": r.iterations, "outer": r.outer,
+             "rel_residual": r.rel_residual} for r in rep]
+
+
+_SOLVE_OK = (FE_OK, FE_ERR_NOT_CONVERGED, FE_ERR_BREAKDOWN)
+
+
+def fe_solve_batch(ctx, system, waves, n_dof: int, opts: fe_solve_opts | None = None, x_out=None,
+                   x_on_device: bool = False, raise_on_fail: bool = True):
+    """Solves A X = B(waves).  x_out: None (a host array is returned), a host
+    numpy array [n_dof, R] complex128, or a device address.  Returns
+    (status, x, reports)."""
+    arr = planewave_array(waves)
+    R = len(arr)
+    opts = opts or solve_opts()
+    rep = (fe_solve_report * R)()
+    if x_out is None:
+        x_out = np.empty((n_dof, R), np.complex128)
+        x_on_device = False
+    st = load().fe_solve_batch(ctx, system, R, arr, C.byref(opts), _ptr(x_out), 1 if x_on_device else 0, rep)
+    _check(st, "fe_solve_batch", ok=(FE_OK,) if raise_on_fail else _SOLVE_OK)
+    return st, x_out, _reports(rep)
+
+
+def fe_solve_rhs(ctx, system, b, nrhs: int, opts: fe_solve_opts | None = None, x_out=None,
+                 b_on_device=False, x_on_device=False, use_x0=False, raise_on_fail=True):
+    opts = opts or solve_opts()
+    rep = (fe_solve_report * nrhs)()
+    if x_out is None:
+        x_out = np.zeros((np.asarray(b).shape[0], nrhs), np.complex128)
+        x_on_device = False
+    if not b_on_device:
+        b = np.ascontiguousarray(b, dtype=np.complex128)
+    st = load().fe_solve_rhs(ctx, system, int(nrhs), _ptr(b), 1 if b_on_device else 0, C.byref(opts),
+                             _ptr(x_out), 1 if x_on_device else 0, 1 if use_x0 else 0, rep)
+    _check(st, "fe_solve_rhs", ok=(FE_OK,) if raise_on_fail else _SOLVE_OK)
+    return st, x_out, _reports(rep)

@@ -1,5 +1,11 @@
+import os
 import sys
 from pathlib import Path
+
+# The oracle's sparse LU and BLAS calls run single-threaded: predictable
+# timings, no oversubscription when tests run beside other CPU work.
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
 
 import pytest
 
@@ -28,6 +34,9 @@ def ctx(fe):
     if not torch.cuda.is_available():
         pytest.fail("GPU test without a CUDA device: run these with -m gpu on a GPU machine")
     torch.cuda.init()
-    c = fe.fe_ctx_create(0)
+    stream = torch.cuda.Stream()
+    c = fe.fe_ctx_create(0, stream=stream.cuda_stream)
+    c.torch_stream = stream
     yield c
+    fe.fe_ctx_synchronize(c)
     fe.fe_ctx_destroy(c)
