@@ -83,7 +83,7 @@ typedef enum fe_precision {
 typedef struct fe_options {
     void* stream;      /* cudaStream_t for all work of the context; NULL = context-owned stream */
     int32_t variant;   /* fe_variant; default FE_VARIANT_S */
-    double abc_sigma;  /* weight of the transverse ABC term: -1 dispersion-consistent (default), +1 literal Eq. 3, 0 first order */
+    double abc_sigma;  /* weight of the transverse ABC term: +1 Eq. 3 as printed (default, absorbing for every mode), -1 Taylor sign, 0 first order */
     double penalty_s;  /* grad-div penalty coefficient s (Eq. 2); default 1 */
 } fe_options;
 

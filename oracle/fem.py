@@ -31,12 +31,16 @@ finite element method", Section 2):
 * variants: 'S' = a + G (complex symmetric), 'L' = a + L + G (literal Eq. 4),
   'P' = (A_L + A_L^T)/2 (the symmetrisation by the transpose of Section 3.1.4).
 
-Readings of the paper used here (sign of the mass term, sign of the ABC
-Laplacian, penalty coefficient, PEC treatment) are the ones listed in the
-design notes: mass term -k0^2 mu_r (Eq. 1), sigma = -1 (dispersion-consistent
-reading of Eq. 3), s = 1 (Eq. 4 shows no coefficient), PEC elements are not
-meshed and PEC faces carry only L (Section 3.1.3: the H formulation needs no
-conductor condition).
+Readings of the paper used here: mass term -k0^2 mu_r (Eq. 1; Eq. 4 prints
++, which turns the Helmholtz operator into a non-oscillatory one); sigma = +1,
+Eq. 3 as printed (g = j k0 H_t - (j/2k0) lap_t H_t, whose weak form adds
++ (j/2k0) int grad_t W : grad_t H): the imaginary part of G is then positive
+for every tangential mode, i.e. the boundary absorbs; the opposite sign
+(sigma = -1, the sign a Taylor expansion of the normal wavenumber suggests)
+makes k0 M - K/(2k0) negative for tangential wavenumbers above sqrt(2) k0,
+an active boundary for most mesh modes; s = 1 (Eq. 4 shows no coefficient);
+PEC elements are not meshed and PEC faces carry only L (Section 3.1.3: the H
+formulation needs no conductor condition).
 
 Element integrals use 2x2x2 Gauss-Legendre points (exact for products of
 trilinear functions); face integrals 2x2 points.  Assembly is a plain
@@ -183,7 +187,7 @@ def _face_parts(h, face):
     return mt, kt, pn
 
 
-def face_abc_matrix(h, face, k0, sigma=-1.0):
+def face_abc_matrix(h, face, k0, sigma=1.0):
     """24x24 (element-local) matrix of the weak Engquist-Majda form G (Eq. 3)."""
     mt, kt, _ = _face_parts(tuple(float(v) for v in h), face)
     return 1j * k0 * mt + sigma * (1j / (2.0 * k0)) * kt
@@ -195,7 +199,7 @@ def face_penalty_matrix(h, face, s=1.0):
     return -s * pn
 
 
-def face_rhs(h, face, elem_corner, k0, k_hat, p_hat, amp, sigma=-1.0):
+def face_rhs(h, face, elem_corner, k0, k_hat, p_hat, amp, sigma=1.0):
     """Right-hand side of Eq. 4 on outer faces of one orientation, [F, 24, R]:
     b[f, 3a+alpha, r] = G(N_a e_alpha, H_i) - int N_a e_alpha . (n x curl H_i) ds
     for H_i = p_hat[r] amp[r] exp(-j k0 k_hat[r] . x); elem_corner[f] = world
@@ -342,7 +346,7 @@ def _coo_add(rows, cols, vals, dofs, mat_block):
     vals.append(np.broadcast_to(mat_block.ravel(), (n, 576)).ravel())
 
 
-def assemble(problem, variant="S", sigma=-1.0, s=1.0, maps=None, chunk=20000):
+def assemble(problem, variant="S", sigma=1.0, s=1.0, maps=None, chunk=20000):
     """Global n_dof x n_dof complex128 CSR matrix of Eq. 4's left-hand side.
 
     Element matrices are summed into the global matrix entry by entry
@@ -405,7 +409,7 @@ def element_corner(problem, e):
     return o + np.stack([i, j, k], axis=-1).astype(float) * h
 
 
-def rhs(problem, waves, sigma=-1.0, maps=None):
+def rhs(problem, waves, sigma=1.0, maps=None):
     """B[n_dof, R]: right-hand side of Eq. 4 for each plane wave, summed over
     the outer (Sext) faces."""
     maps = maps if maps is not None else mesh_maps(problem)

@@ -142,7 +142,7 @@ void fe_options_default(fe_options* opt) {
     if (!opt) return;
     opt->stream = nullptr;
     opt->variant = FE_VARIANT_S;
-    opt->abc_sigma = -1.0;
+    opt->abc_sigma = 1.0;
     opt->penalty_s = 1.0;
 }
 

@@ -153,7 +153,7 @@ def _ptr(a) -> int:
 
 # --------------------------------------------------------------------------
 def fe_ctx_create(device: int = 0, stream: int | None = None, variant: int = FE_VARIANT_S,
-                  abc_sigma: float = -1.0, penalty_s: float = 1.0):
+                  abc_sigma: float = 1.0, penalty_s: float = 1.0):
     lib = load()
     opt = fe_options()
     lib.fe_options_default(C.byref(opt))

@@ -14,7 +14,7 @@ import numpy as np
 ROOT = Path(__file__).resolve().parents[2]
 sys.path.insert(0, str(ROOT))
 
-from oracle import fem  # noqa: E402
+from oracle import fem, krylov  # noqa: E402
 from paper_0704_2344_gb300 import workloads as W  # noqa: E402
 
 
@@ -27,8 +27,12 @@ def main():
     X = fem.solve_direct(A, B)
     res = fem.true_relative_residual(A, X, B)
     print("config 2: n_dof", maps.n_dof, "solve s", round(time.time() - t, 1), "residual", res)
+    t = time.time()
+    xc, its, _ = krylov.cocg(A, B[:, 0], tol=1e-8)
+    t_cocg = time.time() - t
+    print("oracle COCG: iterations", its, "s", round(t_cocg, 1))
     np.savez_compressed(Path(__file__).with_name("config2_x.npz"), x=X.astype(np.complex64),
-                        residual=res, n_dof=maps.n_dof)
+                        residual=res, n_dof=maps.n_dof, cocg_iterations=its, cocg_seconds=t_cocg)
 
 
 if __name__ == "__main__":

@@ -40,4 +40,4 @@ def test_option_defaults_without_gpu(fe):
     import ctypes
     opt = fe.fe_options()
     fe.load().fe_options_default(ctypes.byref(opt))
-    assert opt.variant == fe.FE_VARIANT_S and opt.abc_sigma == -1.0 and opt.penalty_s == 1.0
+    assert opt.variant == fe.FE_VARIANT_S and opt.abc_sigma == 1.0 and opt.penalty_s == 1.0

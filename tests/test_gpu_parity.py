@@ -101,11 +101,17 @@ def _check_values(fe, ctx, prob, variant="S", A=None, maps=None):
     scale = _row_scale(ref, maps)
     err = np.abs(g["c128"] - ref) / scale
     assert err.max() <= 1e-12, err.max()
+    # the complex64 copy is exactly the round-to-nearest of the complex128 values
+    assert np.array_equal(g["c64"], g["c128"].astype(np.complex64))
+    # and within one ulp of the oracle value rounded to complex64, wherever the
+    # value is not rounding noise of a cancelling sum (|ref| > 1e-12 row scale)
     r32 = ref.astype(np.complex64)
     for part in (np.real, np.imag):
         d = np.abs(part(g["c64"]).astype(np.float64) - part(r32).astype(np.float64))
         ulp = np.spacing(np.abs(part(r32))).astype(np.float64)
-        assert np.all(d <= ulp), d.max()
+        significant = np.abs(part(ref)) > 1e-12 * scale
+        assert np.all(d[significant] <= ulp[significant]), d[significant].max()
+        assert np.all(np.abs(part(g["c64"]))[~significant] <= 2e-12 * np.broadcast_to(scale, d.shape)[~significant])
     dref = krylov.block_jacobi_inverse(A)
     derr = np.abs(g["dinv"] - dref).reshape(len(dref), -1).max(axis=1) / np.abs(dref).reshape(len(dref), -1).max(axis=1)
     assert derr.max() <= 1e-10, derr.max()
