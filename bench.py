@@ -109,22 +109,27 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def algorithmic_bytes(info, inner_iters, passes, R=1):
-    """Bytes the method must move per persistent solve launch (complex64
-    inner loop, FP64 refinement), at R right-hand sides:
-      inner iteration: complex64 matrix nnzb*(9*8 + 4) + row pointers, the
-        block-Jacobi inverse n*9*8, and 12 vector passes of n_dof*R*8 B
-        (SpMV: p in, q out; update: p, q, d, r in, d, r, z out; p = z + beta p:
-        z, p in, p out);
-      refinement pass: complex128 matrix nnzb*(9*16 + 4) + row pointers,
-        x and b in, r out (3 * 16 B per dof and column), inner start (r64 in,
-        r, z, p, d out: 16 + 4*8 B), block inverse, x update (d in, x in/out:
-        8 + 32 B)."""
+def algorithmic_bytes(info, inner_iters, passes, R=1, mixed=True):
+    """Bytes the method must move per persistent solve launch, R right-hand
+    sides (s = 8 B per complex64, 16 B per complex128 entry):
+      inner iteration: the matrix in the inner precision nnzb*(9*s + 4) plus
+        row pointers; per dof and column, the sparse product reads u (s) and
+        writes w (s) and the fused dots read r and u (2*16); the update reads
+        u, p, s, d, r (5*16) and w (s), writes p, s, d, r, u (5*16) and the
+        inner-precision copy of u (s, mixed only), and reads the FP64
+        block-Jacobi row (3*16);
+      refinement pass: complex128 matrix nnzb*(9*16 + 4) + row pointers, x
+        and b in, r out (3*16 per dof and column), inner start (r in, 16;
+        r, u, d, p, s out, 5*16; u copy, s; block row 3*16), x update (d in,
+        x in/out: 3*16)."""
     nnzb, n, n_dof = info["nnzb"], info["n_nodes"], info["n_dof"]
     ptr = (n + 1) * 4
-    inner = nnzb * (9 * 8 + 4) + ptr + n * 72 + 12 * n_dof * R * 8
-    outer = nnzb * (9 * 16 + 4) + ptr + n * 72 + n_dof * R * (48 + 48 + 40)
-    return inner_iters * inner / max(R, 1) * R + passes * outer, inner, outer
+    s = 8 if mixed else 16
+    per_dof_inner = (s + s + 32) + (80 + s + 80 + (s if mixed else 0) + 48)
+    inner = nnzb * (9 * s + 4) + ptr + n_dof * R * per_dof_inner
+    per_dof_outer = 48 + (16 + 80 + (s if mixed else 0) + 48) + 48
+    outer = nnzb * (9 * 16 + 4) + ptr + n_dof * R * per_dof_outer
+    return inner_iters * inner + passes * outer, inner, outer
 
 
 def run_ours(args, rank, world, local_rank):
@@ -213,7 +218,7 @@ def run_ours(args, rank, world, local_rank):
         t = torch.tensor([ms_local], device=f"cuda:{local_rank}", dtype=torch.float64)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
-    alg, inner_b, outer_b = algorithmic_bytes(info, inner_iters, passes, R)
+    alg, inner_b, outer_b = algorithmic_bytes(info, inner_iters / R, passes, R, precision == fe.FE_PREC_MIXED)
     achieved = alg / (kernel_ms * 1e-3) / 1e9 if kernel_ms > 0 else None
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     peak = peaks.get("hbm_gbs", 6800.0)

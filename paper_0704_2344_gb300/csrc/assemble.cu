@@ -15,7 +15,9 @@
 // the diagonal block for the block-Jacobi preconditioner.
 #include "fe_internal.cuh"
 
+#include <cstring>
 #include <new>
+#include <vector>
 
 namespace fe {
 
@@ -137,7 +139,8 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                                                   const int* __restrict__ row_ptr,
                                                   const double2* __restrict__ tab, double2* __restrict__ val64,
                                                   float2* __restrict__ val32, double2* __restrict__ dinv64,
-                                                  float2* __restrict__ dinv32, int n_act, int* __restrict__ status) {
+                                                  float2* __restrict__ dinv32, int n_act, int64_t stride,
+                                                  int* __restrict__ status) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_act) return;
@@ -209,13 +212,12 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
             }
         }
     }
-    double2* o64 = val64 + (size_t)slot * 9;
 #pragma unroll
-    for (int q = 0; q < 9; ++q) o64[q] = acc[q];
+    for (int q = 0; q < 9; ++q) val64[q * stride + slot] = acc[q];
     if (val32) {
-        float2* o32 = val32 + (size_t)slot * 9;
 #pragma unroll
-        for (int q = 0; q < 9; ++q) o32[q] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
+        for (int q = 0; q < 9; ++q)
+            val32[q * stride + slot] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
     }
     if (lane == 13) {  // diagonal block: 3x3 complex inverse by cofactors
         Cx A[3][3];
@@ -298,10 +300,11 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
     fe_status e;
     const int n_tab = m->n_mat + 12;
     if ((e = dev_alloc(st, s->tables, (size_t)n_tab * 576 * sizeof(double2))) != FE_OK) return fail(e);
-    if ((e = dev_alloc(st, s->val64, (size_t)m->nnzb * 9 * sizeof(double2))) != FE_OK) return fail(e);
+    s->stride = ((int64_t)m->nnzb + 63) / 64 * 64;
+    if ((e = dev_alloc(st, s->val64, (size_t)s->stride * 9 * sizeof(double2))) != FE_OK) return fail(e);
     if ((e = dev_alloc(st, s->dinv64, (size_t)m->n_act * 9 * sizeof(double2))) != FE_OK) return fail(e);
     if (precision == FE_PREC_MIXED) {
-        if ((e = dev_alloc(st, s->val32, (size_t)m->nnzb * 9 * sizeof(float2))) != FE_OK) return fail(e);
+        if ((e = dev_alloc(st, s->val32, (size_t)s->stride * 9 * sizeof(float2))) != FE_OK) return fail(e);
         if ((e = dev_alloc(st, s->dinv32, (size_t)m->n_act * 9 * sizeof(float2))) != FE_OK) return fail(e);
     }
     TableParams P{};
@@ -332,7 +335,7 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
                                            (const int*)m->node_id.ptr, (const int*)m->row_ptr.ptr,
                                            (const double2*)s->tables.ptr, (double2*)s->val64.ptr,
                                            (float2*)s->val32.ptr, (double2*)s->dinv64.ptr, (float2*)s->dinv32.ptr,
-                                           m->n_act, d_status);
+                                           m->n_act, s->stride, d_status);
     {
         count_launches(1);
         cudaError_t ce = cudaGetLastError();
@@ -356,12 +359,19 @@ fe_status fe_system_export(fe_ctx* ctx, const fe_system* s, void* vals_c128, voi
     }
     cudaStream_t st = ctx->stream;
     const fe_mesh* m = s->mesh;
-    if (vals_c128)
-        FE_CUDA(cudaMemcpyAsync(vals_c128, s->val64.ptr, (size_t)m->nnzb * 9 * sizeof(double2),
-                                cudaMemcpyDeviceToHost, st));
-    if (vals_c64)
-        FE_CUDA(cudaMemcpyAsync(vals_c64, s->val32.ptr, (size_t)m->nnzb * 9 * sizeof(float2),
-                                cudaMemcpyDeviceToHost, st));
+    // planes -> [nnzb][9] (host-side reorder; export is for checks, not the hot path)
+    auto export_planes = [&](void* dst, const void* src, size_t elem) -> fe_status {
+        std::vector<char> tmp((size_t)s->stride * 9 * elem);
+        FE_CUDA(cudaMemcpyAsync(tmp.data(), src, tmp.size(), cudaMemcpyDeviceToHost, st));
+        FE_CUDA(cudaStreamSynchronize(st));
+        char* out = (char*)dst;
+        for (int64_t b = 0; b < m->nnzb; ++b)
+            for (int q = 0; q < 9; ++q)
+                memcpy(out + ((size_t)b * 9 + q) * elem, tmp.data() + ((size_t)q * s->stride + b) * elem, elem);
+        return FE_OK;
+    };
+    if (vals_c128) FE_TRY(export_planes(vals_c128, s->val64.ptr, sizeof(double2)));
+    if (vals_c64) FE_TRY(export_planes(vals_c64, s->val32.ptr, sizeof(float2)));
     if (dinv_c128)
         FE_CUDA(cudaMemcpyAsync(dinv_c128, s->dinv64.ptr, (size_t)m->n_act * 9 * sizeof(double2),
                                 cudaMemcpyDeviceToHost, st));

@@ -95,6 +95,10 @@ struct fe_system {
     int variant = FE_VARIANT_S;
     double sigma = -1, s_pen = 1;
     fe::DevBuf tables;               // double2 [(n_mat + 12) * 576], block-major
-    fe::DevBuf val64, val32;         // double2 / float2 [nnzb * 9]
+    // Block values are stored as 9 planes, one per block entry (alpha, beta):
+    // value (alpha, beta) of block s at [(3*alpha + beta) * stride + s], so a
+    // warp reading one entry of consecutive blocks reads consecutive memory.
+    int64_t stride = 0;              // plane stride: nnzb rounded up to a multiple of 64
+    fe::DevBuf val64, val32;         // double2 / float2 [9 * stride]
     fe::DevBuf dinv64, dinv32;       // double2 / float2 [n_act * 9]
 };

@@ -37,43 +37,88 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
     return t;
 }
 
-// Warp-per-row product of one block row with a single vector (R = 1): lanes
-// walk the row's 9*(s1-s0) complex entries in order, so every load of the
-// matrix is a coalesced 32-entry stretch; each lane accumulates into the
-// output component alpha of its entry, then a butterfly leaves the three
-// row results in every lane.
-template <typename C, bool kCoherentX>
-__device__ __forceinline__ void row_product_r1(const C* __restrict__ val, const int* __restrict__ col, int s0, int s1,
-                                               const C* x, int lane, C& y0, C& y1, C& y2) {
+}  // namespace fe
+
+namespace fe {
+
+// ---------------------------------------------------------------------------
+// Bulk (TMA) copies global -> shared completed on an mbarrier.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* mbar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(mbar)), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* mbar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(mbar)), "r"(bytes)
+                 : "memory");
+}
+
+// dst, src 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(mbar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(mbar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the mbarrier; gives up after timeout_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parity, unsigned long long timeout_ns) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    const unsigned long long t0 = globaltimer_ns();
+    while (!mbar_try_wait(mbar, parity)) {
+        if (globaltimer_ns() - t0 > timeout_ns) return false;
+    }
+    return true;
+}
+
+// Orders this thread's earlier generic-proxy accesses (and those it has
+// acquired from other threads) before its later async-proxy (bulk copy)
+// accesses, for global and shared memory.
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
+
+// Row product for a single vector (block values in 9 planes of `stride`
+// entries): lane l < nb = s1 - s0 owns block s0 + l
+// (column index `mycol`, loaded by the caller, possibly one row ahead): it
+// loads the block's 9 complex entries and the 3 entries of x at its column,
+// accumulates the 3x3 block product into fixed accumulators, and a butterfly
+// over the warp adds the blocks of the row.  `xs` is indexed by vector entry
+// minus `xoff` (a shared-memory halo copy, or global memory with xoff = 0).
+template <typename C, bool kShared>
+__device__ __forceinline__ void row_product_r1x(const C* __restrict__ val, int64_t stride, int mycol, int s0, int s1,
+                                                const C* xs, int xoff, int lane, C& y0, C& y1, C& y2) {
     using Tr = decltype(C{}.x);
     Tr a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
-    int slot = s0 + lane / 9;
-    int w = lane % 9;
-    const int end = s1 * 9;
-#pragma unroll 4
-    for (int e = s0 * 9 + lane; e < end; e += 32) {
-        const C v = ld_ro(val + e);
-        const int c = __ldg(col + slot);
-        const int al = w / 3;
-        const int be = w - 3 * al;
-        const C xv = kCoherentX ? ld_cg(x + 3 * c + be) : ld_ro(x + 3 * c + be);
-        const Tr pr = v.x * xv.x - v.y * xv.y;
-        const Tr pi = v.x * xv.y + v.y * xv.x;
-        if (al == 0) {
-            a0r += pr;
-            a0i += pi;
-        } else if (al == 1) {
-            a1r += pr;
-            a1i += pi;
-        } else {
-            a2r += pr;
-            a2i += pi;
-        }
-        w += 5;  // 32 = 3*9 + 5
-        slot += 3;
-        if (w >= 9) {
-            w -= 9;
-            slot += 1;
+    if (lane < s1 - s0) {
+        const C* v = val + s0 + lane;  // plane q at v + q * stride: consecutive lanes, consecutive blocks
+        C m[9];
+#pragma unroll
+        for (int q = 0; q < 9; ++q) m[q] = ld_ro(v + q * stride);
+        const int xi = 3 * mycol - xoff;
+        C x[3];
+#pragma unroll
+        for (int be = 0; be < 3; ++be) x[be] = kShared ? xs[xi + be] : ld_cg(xs + xi + be);
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+            a0r += m[be].x * x[be].x - m[be].y * x[be].y;
+            a0i += m[be].x * x[be].y + m[be].y * x[be].x;
+            a1r += m[3 + be].x * x[be].x - m[3 + be].y * x[be].y;
+            a1i += m[3 + be].x * x[be].y + m[3 + be].y * x[be].x;
+            a2r += m[6 + be].x * x[be].x - m[6 + be].y * x[be].y;
+            a2i += m[6 + be].x * x[be].y + m[6 + be].y * x[be].x;
         }
     }
 #pragma unroll
@@ -90,27 +135,36 @@ __device__ __forceinline__ void row_product_r1(const C* __restrict__ val, const 
     y2 = mk(a2r, a2i);
 }
 
-// Product of one block row with column c of a multi-vector X [n_dof][ldx]:
-// one lane per (row, column).
-template <typename C, bool kCoherentX>
-__device__ __forceinline__ void row_product_col(const C* __restrict__ val, const int* __restrict__ col, int s0, int s1,
-                                                const C* x, int ldx, int c, C& y0, C& y1, C& y2) {
+// FP64 reciprocal (CUDA's round-to-nearest intrinsic).
+__device__ __forceinline__ double rcp64(double x) { return __drcp_rn(x); }
+
+// Row product for column c of a multi-vector (ldx columns), one lane per
+// (row, column).  The next block's column index is loaded while the current
+// block is multiplied, so each block costs one memory round trip.
+template <typename C, bool kShared>
+__device__ __forceinline__ void row_product_colx(const C* __restrict__ val, int64_t stride, const int* __restrict__ col,
+                                                 int s0, int s1, const C* xs, int xoff, int ldx, int c, C& y0, C& y1,
+                                                 C& y2) {
     using Tr = decltype(C{}.x);
     Tr a[6] = {0, 0, 0, 0, 0, 0};
+    int cb = s1 > s0 ? __ldg(col + s0) : 0;
     for (int s = s0; s < s1; ++s) {
-        const int cb = __ldg(col + s);
+        const int cb_next = __ldg(col + min(s + 1, s1 - 1));
         C xv[3];
 #pragma unroll
-        for (int be = 0; be < 3; ++be)
-            xv[be] = kCoherentX ? ld_cg(x + (size_t)(3 * cb + be) * ldx + c) : ld_ro(x + (size_t)(3 * cb + be) * ldx + c);
+        for (int be = 0; be < 3; ++be) {
+            const int xi = (3 * cb + be) * ldx + c - xoff;
+            xv[be] = kShared ? xs[xi] : ld_cg(xs + xi);
+        }
 #pragma unroll
         for (int al = 0; al < 3; ++al)
 #pragma unroll
             for (int be = 0; be < 3; ++be) {
-                const C v = ld_ro(val + (size_t)s * 9 + 3 * al + be);
+                const C v = ld_ro(val + (3 * al + be) * stride + s);
                 a[2 * al] += v.x * xv[be].x - v.y * xv[be].y;
                 a[2 * al + 1] += v.x * xv[be].y + v.y * xv[be].x;
             }
+        cb = cb_next;
     }
     y0 = mk(a[0], a[1]);
     y1 = mk(a[2], a[3]);

@@ -17,12 +17,16 @@
 #include "krylov.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <new>
 
 namespace fe {
 
-constexpr int kThreads = 512;
+constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
+constexpr int kMaxNV = 5;     // reduced values per column and barrier
+constexpr int kTraceIters = 64;
+constexpr int kTracePhases = 8;
 
 struct SyncState {
     unsigned count;
@@ -31,47 +35,60 @@ struct SyncState {
     int pad;
 };
 
+// Inner-loop storage.  The recurrences (d, r, u, p, s) and all inner
+// products are FP64; the matrix, the preconditioner and the sparse product
+// run in the matrix precision TM (complex64 in the mixed mode), on a TM copy
+// uM of u.  The FP64 recurrences are what keeps the Krylov loop converging:
+// with complex64 recurrences the loop stalls on these indefinite systems.
 struct SolveParams {
     int n_rows, n_cta;
     const int* rp;
     const int* col;
     const double2* val64;
-    const void* valT;
-    const void* dinvT;
+    const void* valM;       // matrix in the inner precision
+    int64_t stride;         // plane stride of the block values
+    const double2* dinv64;  // block-Jacobi inverse (FP64: the preconditioner is applied in FP64)
     const double2* b;
     double2* x;
     double2* r64;
-    void* d;
-    void* r;
-    void* z;
-    void* p;
-    void* q;
+    double2* d;
+    double2* r;
+    double2* u;
+    double2* p;
+    double2* s;
+    void* uM;  // u rounded to the inner precision (aliases u when TM = double)
+    void* w;   // w = A uM in the inner precision
     SyncState* sync;
     double* partial;
     double* result;
     double tol, inner_tol;
-    int max_iter, max_outer, use_x0, pad;
+    int max_iter, max_outer, use_x0;
+    int halo;       // bound on |column rank - row rank|
+    int stage;      // stage the CTA's uM halo in shared memory (1) or gather from L2 (0)
+    int red_bytes;  // dynamic shared memory used by the column sums
     int* rep_status;
     int* rep_iters;
     int* rep_outer;
     double* rep_rel;
+    unsigned long long* trace;  // optional [n_cta][kTraceIters][kTracePhases] timestamps
     unsigned long long timeout_ns;
+    unsigned spin_ns;           // back-off between polls of the barrier generation
 };
 
 // ---------------------------------------------------------------------------
-// Grid barrier with fused reduction.  Every CTA writes NV partial values,
-// arrives on a counter; the last arrival sums the partials of all CTAs in
-// CTA order (lane-strided, then a fixed butterfly), publishes the NV results
-// and bumps the generation.  Waits are bounded by P.timeout_ns; on expiry the
-// CTA records kDevTimeout and every CTA leaves at its next barrier.
+// Grid barrier with fused reduction.  Every CTA writes NV partial values and
+// arrives on a counter; the last arrival sums the partials of all CTAs in CTA
+// order (lane-strided, then a fixed butterfly), publishes the NV results and
+// bumps the generation.  One thread per CTA fences: the CTA barrier before
+// it makes the whole CTA's writes part of its release (fences are
+// cumulative).  Waits are bounded by P.timeout_ns; on expiry the CTA records
+// kDevTimeout and every CTA leaves at its next barrier.
 // ---------------------------------------------------------------------------
 template <int NV>
 __device__ __noinline__ bool grid_reduce(const SolveParams& P, const double* s_in, double* s_out) {
     __shared__ int s_last, s_ok;
-    __shared__ unsigned s_gen;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int v = threadIdx.x; v < NV; v += kThreads) P.partial[(size_t)blockIdx.x * NV + v] = s_in[v];
-    __threadfence();
     __syncthreads();
     volatile unsigned* vgen = &P.sync->gen;
     volatile int* verr = &P.sync->err;
@@ -79,13 +96,27 @@ __device__ __noinline__ bool grid_reduce(const SolveParams& P, const double* s_i
         const unsigned g = *vgen;
         __threadfence();
         const unsigned old = atomicAdd(&P.sync->count, 1u);
-        s_last = old == (unsigned)P.n_cta - 1u;
-        s_gen = g;
         s_ok = 1;
+        s_last = old == (unsigned)P.n_cta - 1u;
+        if (!s_last) {
+            const unsigned long long t0 = globaltimer_ns();
+            while (*vgen == g) {
+                if (*verr) {
+                    s_ok = 0;
+                    break;
+                }
+                if (globaltimer_ns() - t0 > P.timeout_ns) {
+                    atomicCAS(&P.sync->err, 0, kDevTimeout);
+                    s_ok = 0;
+                    break;
+                }
+                if (P.spin_ns) __nanosleep(P.spin_ns);
+            }
+        }
+        __threadfence();
     }
     __syncthreads();
     if (s_last) {
-        __threadfence();
         for (int v = warp; v < NV; v += kWarps) {
             double acc = 0.0;
             for (int c = lane; c < P.n_cta; c += 32) acc += __ldcg(P.partial + (size_t)c * NV + v);
@@ -93,30 +124,14 @@ __device__ __noinline__ bool grid_reduce(const SolveParams& P, const double* s_i
             for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
             if (lane == 0) P.result[v] = acc;
         }
-        __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) {
+            __threadfence();
             atomicExch(&P.sync->count, 0u);
             __threadfence();
             atomicAdd(&P.sync->gen, 1u);
         }
-    } else if (threadIdx.x == 0) {
-        const unsigned long long t0 = globaltimer_ns();
-        while (*vgen == s_gen) {
-            if (*verr) {
-                s_ok = 0;
-                break;
-            }
-            if (globaltimer_ns() - t0 > P.timeout_ns) {
-                atomicCAS(&P.sync->err, 0, kDevTimeout);
-                s_ok = 0;
-                break;
-            }
-            __nanosleep(64);
-        }
-        __threadfence();
     }
-    __syncthreads();
     if (threadIdx.x == 0 && *verr) s_ok = 0;
     for (int v = threadIdx.x; v < NV; v += kThreads) s_out[v] = __ldcg(P.result + v);
     __syncthreads();
@@ -124,27 +139,25 @@ __device__ __noinline__ bool grid_reduce(const SolveParams& P, const double* s_i
 }
 
 // Sum over the CTA of per-thread values, per column (thread t holds column
-// t % R): fixed butterfly inside a warp, then warps in order.
+// t % R): a fixed butterfly inside each warp, then one warp per (value,
+// column) adds the warp totals with a fixed butterfly.
 template <int R, int NV>
 __device__ __forceinline__ void cta_colsum(const double (&v)[NV], double* s_red, double* s_in) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double w[NV];
 #pragma unroll
     for (int k = 0; k < NV; ++k) {
-        w[k] = v[k];
+        double w = v[k];
 #pragma unroll
-        for (int o = 16; o >= R; o >>= 1) w[k] += __shfl_xor_sync(0xffffffffu, w[k], o);
-    }
-    if (lane < R) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) s_red[(k * kWarps + warp) * R + lane] = w[k];
+        for (int o = 16; o >= R; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane < R) s_red[(k * kWarps + warp) * R + lane] = w;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < NV * R; i += kThreads) {
+    for (int i = warp; i < NV * R; i += kWarps) {
         const int k = i / R, c = i % R;
-        double acc = 0.0;
-        for (int ww = 0; ww < kWarps; ++ww) acc += s_red[(k * kWarps + ww) * R + c];
-        s_in[i] = acc;
+        double acc = s_red[(k * kWarps + lane) * R + c];  // kWarps == 32
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) s_in[i] = acc;
     }
     __syncthreads();
 }
@@ -153,48 +166,177 @@ template <typename C>
 __device__ __forceinline__ C cmul(C a, C b) {
     return mk(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
+template <typename C>
+__device__ __forceinline__ C cfma(C a, C b, C c) {  // a * b + c
+    return mk(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
+__device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
+__device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+template <typename C>
+__device__ __forceinline__ C from_c128(double2 a);
+template <>
+__device__ __forceinline__ float2 from_c128<float2>(double2 a) {
+    return to_c64(a);
+}
+template <>
+__device__ __forceinline__ double2 from_c128<double2>(double2 a) {
+    return a;
+}
 
-// z = Dinv r for one node and column (3x3 complex block times 3-vector).
+// z = Dinv r for one node and column (3x3 complex block times 3-vector) in
+// the inner precision C.
 template <typename C>
 __device__ __forceinline__ void apply_dinv(const C* __restrict__ dinv, int node, const C (&r)[3], C (&z)[3]) {
+    C m[9];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) m[q] = ld_ro(dinv + (size_t)node * 9 + q);
 #pragma unroll
     for (int al = 0; al < 3; ++al) {
         C acc = mk(decltype(C{}.x)(0), decltype(C{}.x)(0));
 #pragma unroll
         for (int be = 0; be < 3; ++be) {
-            const C m = ld_ro(dinv + (size_t)node * 9 + 3 * al + be);
-            acc.x += m.x * r[be].x - m.y * r[be].y;
-            acc.y += m.x * r[be].y + m.y * r[be].x;
+            acc.x += m[3 * al + be].x * r[be].x - m[3 * al + be].y * r[be].y;
+            acc.y += m[3 * al + be].x * r[be].y + m[3 * al + be].y * r[be].x;
         }
         z[al] = acc;
     }
 }
 
-template <typename T, int R>
-__global__ void __launch_bounds__(kThreads) k_solve(SolveParams P) {
-    using C = typename CplxT<T>::type;
-    const C* valT = (const C*)P.valT;
-    const C* dinvT = (const C*)P.dinvT;
-    C* vd = (C*)P.d;
-    C* vr = (C*)P.r;
-    C* vz = (C*)P.z;
-    C* vp = (C*)P.p;
-    C* vq = (C*)P.q;
+// Copies vector entries [3*h0*R, 3*h1*R) of v into the CTA's shared halo
+// buffer with one bulk (TMA) copy; sets `shift` so that smem[i + shift]
+// holds v[i].  Returns false when the bounded wait expired.
+template <typename C, int R>
+__device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int r0, int r1, char* halo_buf,
+                                           uint64_t* mbar, unsigned& phase, int& shift) {
+    const int h0 = max(0, r0 - P.halo), h1 = min(P.n_rows, r1 + P.halo);
+    const size_t b0 = (size_t)3 * h0 * R * sizeof(C), b1 = (size_t)3 * h1 * R * sizeof(C);
+    const size_t a0 = b0 & ~(size_t)15, a1 = (b1 + 15) & ~(size_t)15;
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(mbar, (unsigned)(a1 - a0));
+        bulk_g2s(halo_buf, (const char*)v + a0, (unsigned)(a1 - a0), mbar);
+    }
+    bool ok = mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns);
+    if (!ok) {
+        atomicCAS(&P.sync->err, 0, kDevTimeout);
+        mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns);  // let the copy land before leaving
+    }
+    phase += 1;
+    shift = (int)((b0 - a0) / sizeof(C)) - 3 * h0 * R;
+    return ok;
+}
 
-    __shared__ double s_red[3 * kWarps * R];
-    __shared__ double s_in[3 * R], s_out[3 * R];
-    __shared__ double s_rn[R], s_bn[R], s_itol[R], s_rel[R];
-    __shared__ double s_rho_r[R], s_rho_i[R];
-    __shared__ T s_ar[R], s_ai[R], s_br[R], s_bi[R];
+// w = A uM over the CTA's rows (inner precision), with the per-column FP64
+// partial dot products g += r^T u, dl += u^T w, rr += |r|^2 (own rows).
+template <typename TM, int R, bool kStaged>
+__device__ __forceinline__ void spmv_dots(const SolveParams& P, const typename CplxT<TM>::type* xs, int xshift,
+                                          int r0, int r1, double (&acc)[5]) {
+    using C = typename CplxT<TM>::type;
+    const C* valM = (const C*)P.valM;
+    const C* uM = (const C*)P.uM;
+    C* w = (C*)P.w;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (R == 1) {
+        int row = r0 + warp;
+        int s0 = 0, s1 = 1, mycol = 0;
+        if (row < r1) {
+            s0 = __ldg(P.rp + row);
+            s1 = __ldg(P.rp + row + 1);
+            mycol = __ldg(P.col + s0 + min(lane, s1 - s0 - 1));
+        }
+        for (; row < r1; row += kWarps) {
+            // prefetch the next row's extent and column indices
+            const int nrow = row + kWarps;
+            int ns0 = 0, ns1 = 1, ncol = 0;
+            if (nrow < r1) {
+                ns0 = __ldg(P.rp + nrow);
+                ns1 = __ldg(P.rp + nrow + 1);
+                ncol = __ldg(P.col + ns0 + min(lane, ns1 - ns0 - 1));
+            }
+            const int o = 3 * row + (lane < 3 ? lane : 0);
+            const double2 rv = __ldcg(P.r + o);  // issued early, consumed after the product
+            const double2 uv = __ldcg(P.u + o);
+            C y0, y1, y2;
+            row_product_r1x<C, kStaged>(valM, P.stride, mycol, s0, s1, kStaged ? xs : uM, kStaged ? -xshift : 0, lane, y0, y1,
+                                        y2);
+            if (lane < 3) {
+                const C y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
+                w[o] = y;
+                const double2 yd = to_c128(y);
+                acc[0] += rv.x * uv.x - rv.y * uv.y;
+                acc[1] += rv.x * uv.y + rv.y * uv.x;
+                acc[2] += uv.x * yd.x - uv.y * yd.y;
+                acc[3] += uv.x * yd.y + uv.y * yd.x;
+                acc[4] += rv.x * rv.x + rv.y * rv.y;
+            }
+            s0 = ns0;
+            s1 = ns1;
+            mycol = ncol;
+        }
+    } else {
+        constexpr int kRowsPerWarp = 32 / R;
+        const int c = lane % R;
+        for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1; row += kWarps * kRowsPerWarp) {
+            double2 rv[3], uv[3];
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                rv[al] = __ldcg(P.r + (size_t)(3 * row + al) * R + c);
+                uv[al] = __ldcg(P.u + (size_t)(3 * row + al) * R + c);
+            }
+            C y[3];
+            row_product_colx<C, kStaged>(valM, P.stride, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), kStaged ? xs : uM,
+                                         kStaged ? -xshift : 0, R, c, y[0], y[1], y[2]);
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                w[(size_t)(3 * row + al) * R + c] = y[al];
+                const double2 yd = to_c128(y[al]);
+                acc[0] += rv[al].x * uv[al].x - rv[al].y * uv[al].y;
+                acc[1] += rv[al].x * uv[al].y + rv[al].y * uv[al].x;
+                acc[2] += uv[al].x * yd.x - uv[al].y * yd.y;
+                acc[3] += uv[al].x * yd.y + uv[al].y * yd.x;
+                acc[4] += rv[al].x * rv[al].x + rv[al].y * rv[al].y;
+            }
+        }
+    }
+}
+
+#define FE_TRACE_MARK(k)                                                                        \
+    do {                                                                                        \
+        if (P.trace && tid == 0 && trace_it < kTraceIters)                                      \
+            P.trace[((size_t)blockIdx.x * kTraceIters + trace_it) * kTracePhases + (k)] = globaltimer_ns(); \
+    } while (0)
+
+// The persistent solve: FP64 true residual, inner preconditioned COCG in the
+// single-reduction form of Chronopoulos and Gear (one sparse product w = A u
+// and one fused reduction of r^T u, u^T w, ||r||^2 per iteration; two grid
+// barriers), FP64 solution update.
+template <typename TM, int R>
+__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
+    using C = typename CplxT<TM>::type;
+    C* uM = (C*)P.uM;
+    const C* wv = (const C*)P.w;
+
+    extern __shared__ __align__(128) char dyn[];
+    double* s_red = (double*)dyn;
+    char* halo_buf = dyn + P.red_bytes;
+    __shared__ __align__(8) uint64_t s_mbar;
+    __shared__ double s_in[kMaxNV * R], s_out[kMaxNV * R];
+    __shared__ double s_rn[R], s_itol[R], s_rel[R];
+    __shared__ double s_gam_r[R], s_gam_i[R], s_al_r[R], s_al_i[R], s_be_r[R], s_be_i[R];
     __shared__ int s_active[R], s_pass[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_pass_it[R];
     __shared__ int s_any;
+    __shared__ double2 s_exch[kThreads];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const int r0 = (int)((int64_t)blockIdx.x * P.n_rows / P.n_cta);
     const int r1 = (int)((int64_t)(blockIdx.x + 1) * P.n_rows / P.n_cta);
     const int n_items = (r1 - r0) * R;  // (node, column) pairs owned by this CTA
     const int my_c = tid % R;           // column of every item this thread handles
+    unsigned mbar_phase = 0;
+    int trace_it = 0;
 
+    if (tid == 0) mbar_init(&s_mbar, 1);
     if (tid < R) {
         s_done[tid] = 0;
         s_status[tid] = FE_OK;
@@ -213,27 +355,45 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveParams P) {
         // ---- FP64 true residual r = b - A x and the norms ||r||, ||b|| ----
         {
             double acc[2] = {0.0, 0.0};
+            const int lane = tid & 31, warp = tid >> 5;
             if (R == 1) {
-                for (int row = r0 + warp; row < r1; row += kWarps) {
+                int row = r0 + warp;
+                int s0 = 0, s1 = 1, mycol = 0;
+                if (row < r1) {
+                    s0 = __ldg(P.rp + row);
+                    s1 = __ldg(P.rp + row + 1);
+                    mycol = __ldg(P.col + s0 + min(lane, s1 - s0 - 1));
+                }
+                for (; row < r1; row += kWarps) {
+                    const int nrow = row + kWarps;
+                    int ns0 = 0, ns1 = 1, ncol = 0;
+                    if (nrow < r1) {
+                        ns0 = __ldg(P.rp + nrow);
+                        ns1 = __ldg(P.rp + nrow + 1);
+                        ncol = __ldg(P.col + ns0 + min(lane, ns1 - ns0 - 1));
+                    }
+                    const int o = 3 * row + (lane < 3 ? lane : 0);
+                    const double2 bv = __ldg(P.b + o);
                     double2 y0, y1, y2;
-                    row_product_r1<double2, true>(P.val64, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), P.x,
-                                                  lane, y0, y1, y2);
+                    row_product_r1x<double2, false>(P.val64, P.stride, mycol, s0, s1, P.x, 0, lane, y0, y1, y2);
                     if (lane < 3) {
                         const double2 y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-                        const double2 bv = __ldg(P.b + 3 * row + lane);
                         const double2 rv = make_double2(bv.x - y.x, bv.y - y.y);
-                        P.r64[3 * row + lane] = rv;
+                        P.r64[o] = rv;
                         acc[0] += rv.x * rv.x + rv.y * rv.y;
                         acc[1] += bv.x * bv.x + bv.y * bv.y;
                     }
+                    s0 = ns0;
+                    s1 = ns1;
+                    mycol = ncol;
                 }
             } else {
                 constexpr int kRowsPerWarp = 32 / R;
                 const int c = lane % R;
                 for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1; row += kWarps * kRowsPerWarp) {
                     double2 y[3];
-                    row_product_col<double2, true>(P.val64, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), P.x, R,
-                                                   c, y[0], y[1], y[2]);
+                    row_product_colx<double2, false>(P.val64, P.stride, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), P.x,
+                                                     0, R, c, y[0], y[1], y[2]);
 #pragma unroll
                     for (int al = 0; al < 3; ++al) {
                         const size_t o = (size_t)(3 * row + al) * R + c;
@@ -270,7 +430,6 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveParams P) {
                     s_pass[c] = 1;
                     s_pass_it[c] = 0;
                     s_rn[c] = rn;
-                    s_bn[c] = bn;
                     s_itol[c] = fmax(P.inner_tol, 0.5 * P.tol * bn / rn);
                     s_outer[c] += 1;
                 }
@@ -285,162 +444,91 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveParams P) {
         __syncthreads();
         if (!s_any) break;
 
-        // ---- inner start: r = RN(r64 / ||r64||), d = 0, z = Dinv r, p = z ----
+        // ---- inner start: r = r64 / ||r64||, u = Dinv r, d = p = s = 0 ----
         {
-            double acc[2] = {0.0, 0.0};
             const bool act = s_active[my_c];
             const double sc = act ? 1.0 / s_rn[my_c] : 0.0;
             for (int i = tid; i < n_items; i += kThreads) {
                 const int node = r0 + i / R;
-                C rv[3], zv[3];
+                double2 rv[3], uv[3];
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     const double2 w = __ldcg(P.r64 + (size_t)(3 * node + al) * R + my_c);
-                    rv[al] = mk((T)(w.x * sc), (T)(w.y * sc));
+                    rv[al] = make_double2(w.x * sc, w.y * sc);
                 }
-                apply_dinv(dinvT, node, rv, zv);
-                T ar = 0, ai = 0;
+                apply_dinv(P.dinv64, node, rv, uv);
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     const size_t o = (size_t)(3 * node + al) * R + my_c;
-                    if (!act) zv[al] = mk((T)0, (T)0);
-                    vr[o] = rv[al];
-                    vz[o] = zv[al];
-                    vp[o] = zv[al];
-                    vd[o] = mk((T)0, (T)0);
-                    ar += rv[al].x * zv[al].x - rv[al].y * zv[al].y;
-                    ai += rv[al].x * zv[al].y + rv[al].y * zv[al].x;
+                    P.r[o] = rv[al];
+                    P.u[o] = uv[al];
+                    if (sizeof(C) != sizeof(double2)) uM[o] = from_c128<C>(uv[al]);
+                    P.d[o] = make_double2(0.0, 0.0);
+                    P.p[o] = make_double2(0.0, 0.0);
+                    P.s[o] = make_double2(0.0, 0.0);
                 }
-                acc[0] += (double)ar;
-                acc[1] += (double)ai;
             }
-            cta_colsum<R, 2>(acc, s_red, s_in);
-            if (!grid_reduce<2 * R>(P, s_in, s_out)) goto out;
-            if (tid < R) {
-                s_rho_r[tid] = s_out[tid];
-                s_rho_i[tid] = s_out[R + tid];
-            }
-            __syncthreads();
+            if (!grid_reduce<0>(P, s_in, s_out)) goto out;
         }
 
-        // ---- inner COCG passes ----
-        for (;;) {
-            // q = A p and p^T q
+        // ---- inner iterations ----
+        for (bool first = true;; first = false) {
+            FE_TRACE_MARK(0);
+            // w = A u, gamma = r^T u, delta = u^T w, ||r||^2
             {
-                T pr = 0, pi = 0;
-                if (R == 1) {
-                    for (int row = r0 + warp; row < r1; row += kWarps) {
-                        C y0, y1, y2;
-                        row_product_r1<C, true>(valT, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), vp, lane, y0,
-                                                y1, y2);
-                        if (lane < 3) {
-                            const C y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-                            vq[3 * row + lane] = y;
-                            const C pv = ld_cg(vp + 3 * row + lane);
-                            pr += pv.x * y.x - pv.y * y.y;
-                            pi += pv.x * y.y + pv.y * y.x;
-                        }
-                    }
+                double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+                if (P.stage) {
+                    int shift = 0;
+                    if (!stage_halo<C, R>(P, uM, r0, r1, halo_buf, &s_mbar, mbar_phase, shift)) goto out;
+                    FE_TRACE_MARK(1);
+                    spmv_dots<TM, R, true>(P, (const C*)halo_buf, shift, r0, r1, acc);
                 } else {
-                    constexpr int kRowsPerWarp = 32 / R;
-                    const int c = lane % R;
-                    for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1; row += kWarps * kRowsPerWarp) {
-                        C y[3];
-                        row_product_col<C, true>(valT, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), vp, R, c,
-                                                 y[0], y[1], y[2]);
-#pragma unroll
-                        for (int al = 0; al < 3; ++al) {
-                            const size_t o = (size_t)(3 * row + al) * R + c;
-                            vq[o] = y[al];
-                            const C pv = ld_cg(vp + o);
-                            pr += pv.x * y[al].x - pv.y * y[al].y;
-                            pi += pv.x * y[al].y + pv.y * y[al].x;
-                        }
-                    }
+                    spmv_dots<TM, R, false>(P, nullptr, 0, r0, r1, acc);
                 }
-                double acc[2] = {(double)pr, (double)pi};
-                cta_colsum<R, 2>(acc, s_red, s_in);
-                if (!grid_reduce<2 * R>(P, s_in, s_out)) goto out;
+                FE_TRACE_MARK(2);
+                cta_colsum<R, 5>(acc, s_red, s_in);
+                FE_TRACE_MARK(3);
+                if (!grid_reduce<5 * R>(P, s_in, s_out)) goto out;
+                FE_TRACE_MARK(4);
             }
             if (tid < R) {
                 const int c = tid;
                 if (s_active[c]) {
-                    const double mr = s_out[c], mi = s_out[R + c];
-                    const double den = mr * mr + mi * mi;
-                    if (!(den > 0.0) || !(den < 1e300)) {
-                        s_active[c] = 0;
-                        if (s_pass_it[c] == 0) s_status[c] = FE_ERR_BREAKDOWN;
-                        s_ar[c] = 0;
-                        s_ai[c] = 0;
-                    } else {
-                        // alpha = rho / mu
-                        s_ar[c] = (T)((s_rho_r[c] * mr + s_rho_i[c] * mi) / den);
-                        s_ai[c] = (T)((s_rho_i[c] * mr - s_rho_r[c] * mi) / den);
+                    const double gr = s_out[c], gi = s_out[R + c];
+                    const double dr = s_out[2 * R + c], di = s_out[3 * R + c];
+                    const double nr2 = s_out[4 * R + c];  // ||r||^2
+                    if (!first) {
+                        s_iters[c] += 1;
+                        s_pass_it[c] += 1;
                     }
-                } else {
-                    s_ar[c] = 0;
-                    s_ai[c] = 0;
-                }
-            }
-            __syncthreads();
-            // d += alpha p, r -= alpha q, z = Dinv r, rho' = r^T z, ||r||^2
-            {
-                double acc[3] = {0.0, 0.0, 0.0};
-                if (s_active[my_c]) {
-                    const C alpha = mk(s_ar[my_c], s_ai[my_c]);
-                    T rho_r = 0, rho_i = 0, rr = 0;
-                    for (int i = tid; i < n_items; i += kThreads) {
-                        const int node = r0 + i / R;
-                        C rv[3], zv[3];
-#pragma unroll
-                        for (int al = 0; al < 3; ++al) {
-                            const size_t o = (size_t)(3 * node + al) * R + my_c;
-                            const C pv = ld_cg(vp + o), qv = ld_cg(vq + o);
-                            C dv = ld_cg(vd + o);
-                            C rw = ld_cg(vr + o);
-                            const C ap = cmul(alpha, pv), aq = cmul(alpha, qv);
-                            dv.x += ap.x;
-                            dv.y += ap.y;
-                            rw.x -= aq.x;
-                            rw.y -= aq.y;
-                            vd[o] = dv;
-                            vr[o] = rw;
-                            rv[al] = rw;
-                        }
-                        apply_dinv(dinvT, node, rv, zv);
-#pragma unroll
-                        for (int al = 0; al < 3; ++al) {
-                            vz[(size_t)(3 * node + al) * R + my_c] = zv[al];
-                            rho_r += rv[al].x * zv[al].x - rv[al].y * zv[al].y;
-                            rho_i += rv[al].x * zv[al].y + rv[al].y * zv[al].x;
-                            rr += rv[al].x * rv[al].x + rv[al].y * rv[al].y;
-                        }
-                    }
-                    acc[0] = rho_r;
-                    acc[1] = rho_i;
-                    acc[2] = rr;
-                }
-                cta_colsum<R, 3>(acc, s_red, s_in);
-                if (!grid_reduce<3 * R>(P, s_in, s_out)) goto out;
-            }
-            if (tid < R) {
-                const int c = tid;
-                if (s_active[c]) {
-                    s_iters[c] += 1;
-                    s_pass_it[c] += 1;
-                    const double nr = sqrt(s_out[2 * R + c]);
-                    const double rho_r = s_out[c], rho_i = s_out[R + c];
-                    const double den = s_rho_r[c] * s_rho_r[c] + s_rho_i[c] * s_rho_i[c];
-                    if (!(nr == nr) || nr <= s_itol[c] || s_iters[c] >= P.max_iter || nr > 1e12) {
-                        s_active[c] = 0;
-                    } else if (!(den > 0.0) || (rho_r == 0.0 && rho_i == 0.0)) {
+                    if (!(nr2 == nr2) || nr2 <= s_itol[c] * s_itol[c] || s_iters[c] >= P.max_iter || nr2 > 1e24) {
                         s_active[c] = 0;
                     } else {
-                        // beta = rho' / rho
-                        s_br[c] = (T)((rho_r * s_rho_r[c] + rho_i * s_rho_i[c]) / den);
-                        s_bi[c] = (T)((rho_i * s_rho_r[c] - rho_r * s_rho_i[c]) / den);
-                        s_rho_r[c] = rho_r;
-                        s_rho_i[c] = rho_i;
+                        double br = 0.0, bi = 0.0, er = dr, ei = di;
+                        if (!first) {
+                            // beta = gamma' / gamma;  denominator delta' - beta gamma' / alpha
+                            const double ig = rcp64(s_gam_r[c] * s_gam_r[c] + s_gam_i[c] * s_gam_i[c]);
+                            br = (gr * s_gam_r[c] + gi * s_gam_i[c]) * ig;
+                            bi = (gi * s_gam_r[c] - gr * s_gam_i[c]) * ig;
+                            const double tr = br * gr - bi * gi, ti = br * gi + bi * gr;  // beta gamma'
+                            const double ia = rcp64(s_al_r[c] * s_al_r[c] + s_al_i[c] * s_al_i[c]);
+                            er = dr - (tr * s_al_r[c] + ti * s_al_i[c]) * ia;  // delta' - beta gamma' / alpha
+                            ei = di - (ti * s_al_r[c] - tr * s_al_i[c]) * ia;
+                        }
+                        const double ed = er * er + ei * ei;
+                        const double gg = gr * gr + gi * gi;
+                        if (!(ed > 0.0) || !(ed < 1e300) || !(gg > 0.0)) {
+                            s_active[c] = 0;
+                            if (s_pass_it[c] == 0) s_status[c] = FE_ERR_BREAKDOWN;
+                        } else {
+                            const double ie = rcp64(ed);
+                            s_al_r[c] = (gr * er + gi * ei) * ie;
+                            s_al_i[c] = (gi * er - gr * ei) * ie;
+                            s_be_r[c] = br;
+                            s_be_i[c] = bi;
+                            s_gam_r[c] = gr;
+                            s_gam_i[c] = gi;
+                        }
                     }
                 }
             }
@@ -452,21 +540,52 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveParams P) {
             }
             __syncthreads();
             if (!s_any) break;
-            // p = z + beta p
-            if (s_active[my_c]) {
-                const C beta = mk(s_br[my_c], s_bi[my_c]);
-                for (int i = tid; i < n_items; i += kThreads) {
-                    const int node = r0 + i / R;
-#pragma unroll
-                    for (int al = 0; al < 3; ++al) {
-                        const size_t o = (size_t)(3 * node + al) * R + my_c;
-                        const C pv = ld_cg(vp + o), zv = ld_cg(vz + o);
-                        const C bp = cmul(beta, pv);
-                        vp[o] = mk(zv.x + bp.x, zv.y + bp.y);
+            FE_TRACE_MARK(5);
+            // p = u + beta p; s = w + beta s; d += alpha p; r -= alpha s; u -= alpha Dinv s.
+            // One thread per (dof, column): item i of the CTA is vector entry
+            // 3*r0*R + i; a chunk holds whole nodes, so the three components of
+            // s a node's block-Jacobi product needs are exchanged in shared
+            // memory.
+            {
+                const bool act = s_active[my_c] != 0;
+                const double2 alpha = make_double2(s_al_r[my_c], s_al_i[my_c]);
+                const double2 nalpha = make_double2(-s_al_r[my_c], -s_al_i[my_c]);
+                const double2 beta = make_double2(s_be_r[my_c], s_be_i[my_c]);
+                constexpr int kChunk = (kThreads / (3 * R)) * (3 * R);
+                const int n3 = 3 * n_items;
+                for (int base = 0; base < n3; base += kChunk) {
+                    const int i = base + tid;
+                    const bool valid = act && tid < kChunk && i < n3;
+                    const size_t o = (size_t)3 * r0 * R + i;
+                    double2 ss = make_double2(0.0, 0.0);
+                    if (valid) {
+                        const double2 pp = cfma(beta, __ldcg(P.p + o), __ldcg(P.u + o));
+                        ss = cfma(beta, __ldcg(P.s + o), to_c128(ld_cg(wv + o)));
+                        P.p[o] = pp;
+                        P.s[o] = ss;
+                        P.d[o] = cfma(alpha, pp, __ldcg(P.d + o));
+                        P.r[o] = cfma(nalpha, ss, __ldcg(P.r + o));
                     }
+                    s_exch[tid] = ss;
+                    __syncthreads();
+                    if (valid) {
+                        const int node = r0 + i / (3 * R);
+                        const int al = (i / R) % 3;
+                        const double2* drow = P.dinv64 + (size_t)node * 9 + 3 * al;
+                        double2 q = make_double2(0.0, 0.0);
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) q = cfma(__ldg(drow + be), s_exch[tid + (be - al) * R], q);
+                        const double2 uu = cfma(nalpha, q, __ldcg(P.u + o));
+                        P.u[o] = uu;
+                        if (sizeof(C) != sizeof(double2)) uM[o] = from_c128<C>(uu);
+                    }
+                    __syncthreads();
                 }
             }
+            FE_TRACE_MARK(6);
             if (!grid_reduce<0>(P, s_in, s_out)) goto out;
+            FE_TRACE_MARK(7);
+            ++trace_it;
         }
 
         // ---- FP64 solution update x += ||r|| d ----
@@ -477,10 +596,10 @@ __global__ void __launch_bounds__(kThreads) k_solve(SolveParams P) {
 #pragma unroll
                 for (int al = 0; al < 3; ++al) {
                     const size_t o = (size_t)(3 * node + al) * R + my_c;
-                    const C dv = ld_cg(vd + o);
+                    const double2 dv = __ldcg(P.d + o);
                     double2 xv = P.x[o];
-                    xv.x += sc * (double)dv.x;
-                    xv.y += sc * (double)dv.y;
+                    xv.x += sc * dv.x;
+                    xv.y += sc * dv.y;
                     P.x[o] = xv;
                 }
             }
@@ -500,27 +619,30 @@ out:
 // Standalone products for fe_spmv: y = A x.
 // ---------------------------------------------------------------------------
 template <typename C>
-__global__ void __launch_bounds__(256) k_spmv_r1(const C* __restrict__ val, const int* __restrict__ col,
-                                                 const int* __restrict__ rp, const C* __restrict__ x, C* __restrict__ y,
-                                                 int n_rows) {
+__global__ void __launch_bounds__(256) k_spmv_r1(const C* __restrict__ val, int64_t stride,
+                                                 const int* __restrict__ col, const int* __restrict__ rp,
+                                                 const C* __restrict__ x, C* __restrict__ y, int n_rows) {
     const int lane = threadIdx.x & 31;
     const int nw = (gridDim.x * blockDim.x) >> 5;
     for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nw) {
+        const int s0 = __ldg(rp + row), s1 = __ldg(rp + row + 1);
+        const int mycol = __ldg(col + s0 + min(lane, s1 - s0 - 1));
         C y0, y1, y2;
-        row_product_r1<C, false>(val, col, __ldg(rp + row), __ldg(rp + row + 1), x, lane, y0, y1, y2);
+        row_product_r1x<C, false>(val, stride, mycol, s0, s1, x, 0, lane, y0, y1, y2);
         if (lane < 3) y[3 * row + lane] = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
     }
 }
 
 template <typename C>
-__global__ void __launch_bounds__(256) k_spmv_cols(const C* __restrict__ val, const int* __restrict__ col,
-                                                   const int* __restrict__ rp, const C* __restrict__ x,
-                                                   C* __restrict__ y, int n_rows, int nrhs) {
+__global__ void __launch_bounds__(256) k_spmv_cols(const C* __restrict__ val, int64_t stride,
+                                                   const int* __restrict__ col, const int* __restrict__ rp,
+                                                   const C* __restrict__ x, C* __restrict__ y, int n_rows, int nrhs) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n_rows * nrhs) return;
     const int row = (int)(t / nrhs), c = (int)(t - (int64_t)row * nrhs);
     C v[3];
-    row_product_col<C, false>(val, col, __ldg(rp + row), __ldg(rp + row + 1), x, nrhs, c, v[0], v[1], v[2]);
+    row_product_colx<C, false>(val, stride, col, __ldg(rp + row), __ldg(rp + row + 1), x, 0, nrhs, c, v[0], v[1],
+                               v[2]);
 #pragma unroll
     for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * nrhs + c] = v[al];
 }
@@ -548,22 +670,34 @@ fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewav
                     DevBuf& wave_buf);
 
 struct Workspace {
-    DevBuf b, x, r64, d, r, z, p, q, partial, result, sync, rep;
+    DevBuf b, x, r64, d, r, u, p, s, uM, w, partial, result, sync, rep, trace;
 };
+
+constexpr size_t kSmemBudget = 200 * 1024;
 
 template <typename T, int R>
 static fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
+    static_assert(kWarps == 32, "cta_colsum assumes 32 warps");
+    using C = typename CplxT<T>::type;
+    // one CTA per SM; the reduction scratch and (when it fits) the CTA's
+    // vector halo live in dynamic shared memory
+    P.n_cta = std::min(ctx->num_sms, std::max(1, P.n_rows));
+    P.red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
+    const int64_t rows_per_cta = (P.n_rows + P.n_cta - 1) / P.n_cta + 1;
+    const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
+    P.stage = (P.halo > 0 && (size_t)P.red_bytes + (size_t)halo_bytes <= kSmemBudget) ? 1 : 0;
+    const size_t dyn = (size_t)P.red_bytes + (P.stage ? (size_t)halo_bytes : 0);
+    FE_CUDA(cudaFuncSetAttribute((const void*)k_solve<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
-    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<T, R>, kThreads, 0));
+    FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<T, R>, kThreads, dyn));
     if (per_sm < 1) {
         set_error("solve kernel does not fit on an SM");
         return FE_ERR_CUDA;
     }
-    per_sm = std::min(per_sm, 2);
-    P.n_cta = std::min(per_sm * ctx->num_sms, std::max(1, P.n_rows));
     void* args[] = {&P};
     FE_CUDA(cudaEventRecord(ctx->ev0, ctx->stream));
-    FE_CUDA(cudaLaunchCooperativeKernel((void*)k_solve<T, R>, dim3(P.n_cta), dim3(kThreads), args, 0, ctx->stream));
+    FE_CUDA(cudaLaunchCooperativeKernel((void*)k_solve<T, R>, dim3(P.n_cta), dim3(kThreads), args, dyn,
+                                        ctx->stream));
     FE_CUDA(cudaEventRecord(ctx->ev1, ctx->stream));
     count_launches(1);
     ctx->last_solve.launches += 1;
@@ -604,21 +738,23 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         set_error("mixed-precision solve of a system assembled in FP64 only");
         return FE_ERR_INVALID_ARG;
     }
-    const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
+    const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);  // inner-precision vectors (uM, w)
     Workspace w;
     auto cleanup = [&]() {
-        for (DevBuf* b : {&w.b, &w.x, &w.r64, &w.d, &w.r, &w.z, &w.p, &w.q, &w.partial, &w.result, &w.sync, &w.rep})
+        for (DevBuf* b : {&w.b, &w.x, &w.r64, &w.d, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.w, &w.partial, &w.result,
+                          &w.sync, &w.rep, &w.trace})
             dev_free(st, *b);
     };
     fe_status e = FE_OK;
     const size_t nv = (size_t)n_dof * R;
     const int max_cta = 2 * ctx->num_sms;
     for (auto pr : {std::make_pair(&w.b, nv * sizeof(double2)), std::make_pair(&w.x, nv * sizeof(double2)),
-                    std::make_pair(&w.r64, nv * sizeof(double2)), std::make_pair(&w.d, nv * esz),
-                    std::make_pair(&w.r, nv * esz), std::make_pair(&w.z, nv * esz), std::make_pair(&w.p, nv * esz),
-                    std::make_pair(&w.q, nv * esz),
-                    std::make_pair(&w.partial, (size_t)max_cta * 3 * R * sizeof(double)),
-                    std::make_pair(&w.result, (size_t)3 * R * sizeof(double)),
+                    std::make_pair(&w.r64, nv * sizeof(double2)), std::make_pair(&w.d, nv * sizeof(double2)),
+                    std::make_pair(&w.r, nv * sizeof(double2)), std::make_pair(&w.u, nv * sizeof(double2)),
+                    std::make_pair(&w.p, nv * sizeof(double2)), std::make_pair(&w.s, nv * sizeof(double2)),
+                    std::make_pair(&w.uM, fp64 ? (size_t)16 : nv * esz), std::make_pair(&w.w, nv * esz),
+                    std::make_pair(&w.partial, (size_t)max_cta * kMaxNV * R * sizeof(double)),
+                    std::make_pair(&w.result, (size_t)kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.sync, sizeof(SyncState)),
                     std::make_pair(&w.rep, (size_t)R * (3 * sizeof(int) + sizeof(double)) + 64)}) {
         if ((e = dev_alloc(st, *pr.first, pr.second)) != FE_OK) {
@@ -626,6 +762,13 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
             return e;
         }
     }
+    const bool tracing = getenv("FE_TRACE") && getenv("FE_TRACE")[0] == '1';
+    const size_t trace_bytes = (size_t)ctx->num_sms * kTraceIters * kTracePhases * sizeof(unsigned long long);
+    if (tracing && (e = dev_alloc(st, w.trace, trace_bytes)) != FE_OK) {
+        cleanup();
+        return e;
+    }
+    if (tracing) cudaMemsetAsync(w.trace.ptr, 0, trace_bytes, st);
     std::vector<int> h_rep_i(3 * R);
     std::vector<double> h_rep_d(R);
     fe_status worst = FE_OK;
@@ -645,16 +788,23 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         P.rp = (const int*)m->row_ptr.ptr;
         P.col = (const int*)m->col_idx.ptr;
         P.val64 = (const double2*)s->val64.ptr;
-        P.valT = fp64 ? s->val64.ptr : s->val32.ptr;
-        P.dinvT = fp64 ? s->dinv64.ptr : s->dinv32.ptr;
+        P.valM = fp64 ? s->val64.ptr : s->val32.ptr;
+        P.stride = s->stride;
+        P.dinv64 = (const double2*)s->dinv64.ptr;
         P.b = (const double2*)w.b.ptr;
         P.x = (double2*)w.x.ptr;
         P.r64 = (double2*)w.r64.ptr;
-        P.d = w.d.ptr;
-        P.r = w.r.ptr;
-        P.z = w.z.ptr;
-        P.p = w.p.ptr;
-        P.q = w.q.ptr;
+        P.d = (double2*)w.d.ptr;
+        P.r = (double2*)w.r.ptr;
+        P.u = (double2*)w.u.ptr;
+        P.p = (double2*)w.p.ptr;
+        P.s = (double2*)w.s.ptr;
+        P.uM = fp64 ? w.u.ptr : w.uM.ptr;
+        P.w = w.w.ptr;
+        P.trace = (unsigned long long*)w.trace.ptr;
+        // lexicographic node ranks: a neighbour is at most one plane, one
+        // line and one node away
+        P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
         P.sync = (SyncState*)w.sync.ptr;
         P.partial = (double*)w.partial.ptr;
         P.result = (double*)w.result.ptr;
@@ -669,6 +819,7 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         P.rep_outer = ri + 2 * R;
         P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
         P.timeout_ns = 4000000000ull;
+        P.spin_ns = getenv("FE_SPIN_NS") ? (unsigned)atoi(getenv("FE_SPIN_NS")) : 0u;
         e = fp64 ? dispatch<double>(ctx, R, P) : dispatch<float>(ctx, R, P);
         if (e != FE_OK) break;
         const unsigned gs = (unsigned)((n_dof * nc + 255) / 256);
@@ -686,6 +837,24 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         }
         float ms = 0.0f;
         if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last_solve.kernel_ms += ms;
+        if (tracing) {
+            // per-phase durations (ns) of CTA 0 and the slowest CTA, averaged over traced iterations
+            std::vector<unsigned long long> tr(trace_bytes / sizeof(unsigned long long));
+            cudaMemcpy(tr.data(), w.trace.ptr, trace_bytes, cudaMemcpyDeviceToHost);
+            double sum[kTracePhases] = {0};
+            int n_it = 0;
+            for (int it = 1; it + 1 < kTraceIters; ++it) {
+                const unsigned long long* a = &tr[(size_t)it * kTracePhases];
+                const unsigned long long* b = &tr[(size_t)(it + 1) * kTracePhases];
+                if (!a[0] || !b[0]) break;
+                for (int k = 1; k < kTracePhases; ++k) sum[k] += (double)(a[k] - a[k - 1]);
+                sum[0] += (double)(b[0] - a[kTracePhases - 1]);
+                ++n_it;
+            }
+            fprintf(stderr, "FE_TRACE cta0 %d iterations, ns per phase:", n_it);
+            for (int k = 0; k < kTracePhases; ++k) fprintf(stderr, " %d:%.0f", k, n_it ? sum[k] / n_it : 0.0);
+            fprintf(stderr, "\n");
+        }
         if (hs.err) {
             set_error("solve: a grid barrier wait expired (device status %d)", hs.err);
             e = FE_ERR_TIMEOUT;
@@ -752,12 +921,12 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
     const int* col = (const int*)m->col_idx.ptr;
     if (precision == FE_PREC_FP64) {
         if (nrhs == 1) {
-            k_spmv_r1<double2><<<ctx->num_sms * 8, 256, 0, st>>>((const double2*)s->val64.ptr, col, rp,
+            k_spmv_r1<double2><<<ctx->num_sms * 8, 256, 0, st>>>((const double2*)s->val64.ptr, s->stride, col, rp,
                                                                   (const double2*)x, (double2*)y, m->n_act);
         } else {
             const int64_t n = (int64_t)m->n_act * nrhs;
             k_spmv_cols<double2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                (const double2*)s->val64.ptr, col, rp, (const double2*)x, (double2*)y, m->n_act, nrhs);
+                (const double2*)s->val64.ptr, s->stride, col, rp, (const double2*)x, (double2*)y, m->n_act, nrhs);
         }
     } else if (precision == FE_PREC_MIXED) {
         if (!s->val32.ptr) {
@@ -765,12 +934,12 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
             return FE_ERR_INVALID_ARG;
         }
         if (nrhs == 1) {
-            k_spmv_r1<float2><<<ctx->num_sms * 8, 256, 0, st>>>((const float2*)s->val32.ptr, col, rp,
+            k_spmv_r1<float2><<<ctx->num_sms * 8, 256, 0, st>>>((const float2*)s->val32.ptr, s->stride, col, rp,
                                                                  (const float2*)x, (float2*)y, m->n_act);
         } else {
             const int64_t n = (int64_t)m->n_act * nrhs;
             k_spmv_cols<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-                (const float2*)s->val32.ptr, col, rp, (const float2*)x, (float2*)y, m->n_act, nrhs);
+                (const float2*)s->val32.ptr, s->stride, col, rp, (const float2*)x, (float2*)y, m->n_act, nrhs);
         }
     } else {
         set_error("fe_spmv: bad precision");
