@@ -185,17 +185,24 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
  * Solve (Sections 3.1.5 and 4.2.5: conjugate gradients on the symmetric
  * system with diagonal preconditioning; here the complex-symmetric form,
  * COCG, with 3x3 block-Jacobi preconditioning).  FE_PREC_MIXED runs the
- * Krylov loop in complex64 inside an FP64 iterative refinement: r = b - A x
- * in FP64, inner COCG on A_c64 d = r, x += d, until ||b - A x|| / ||b|| <= tol
- * for every right-hand side.  All right-hand sides are solved together in
- * one persistent device launch per refinement pass.
+ * sparse products of the Krylov loop on the complex64 copy of the matrix
+ * (FP32 arithmetic and accumulation) while the recurrences, inner products
+ * and the preconditioner stay FP64; each time the recursive residual has
+ * dropped by `reliable`, the FP64 true residual b - A x replaces it and the
+ * directions restart (FP64 iterative refinement around complex64 Krylov
+ * passes).  The true residual decides convergence: ||b - A x|| / ||b|| <= tol
+ * for every right-hand side.  Up to
+ * rhs_tile right-hand sides are solved together in one persistent device
+ * launch.
  * ---------------------------------------------------------------------- */
 typedef struct fe_solve_opts {
     int32_t precision;   /* fe_precision; default FE_PREC_MIXED */
     double tol;          /* true FP64 relative residual target; default 1e-8 */
-    double inner_tol;    /* relative reduction per inner (complex64) solve; default 1e-4 */
-    int32_t max_iter;    /* cap on total Krylov iterations per right-hand side; default 20000 */
-    int32_t max_outer;   /* cap on refinement passes; default 30 */
+    double reliable;     /* mixed mode: each time the recursive residual has dropped by this factor since the
+                            last FP64 pass, the FP64 true residual b - A x replaces it and the complex64
+                            Krylov directions restart (iterative refinement); default 1e-4 */
+    int32_t max_iter;    /* cap on Krylov iterations per right-hand side; default 20000 */
+    int32_t max_outer;   /* cap on true-residual replacements per right-hand side; default 200 */
     int32_t rhs_tile;    /* right-hand sides per device pass, 0 = automatic */
 } fe_solve_opts;
 
@@ -204,7 +211,7 @@ void fe_solve_opts_default(fe_solve_opts* o);
 typedef struct fe_solve_report {
     int32_t status;        /* fe_status of this right-hand side */
     int32_t iterations;    /* Krylov iterations (sum over refinement passes) */
-    int32_t outer;         /* refinement passes (true-residual evaluations - 1) */
+    int32_t outer;         /* FP64 true-residual evaluations */
     int32_t reserved;
     double rel_residual;   /* final true FP64 ||b - A x|| / ||b|| */
 } fe_solve_report;

@@ -172,3 +172,56 @@ __device__ __forceinline__ void row_product_colx(const C* __restrict__ val, int6
 }
 
 }  // namespace fe
+
+namespace fe {
+
+// Component alpha of a block row times a single vector: one thread per
+// (row, alpha) walks the row's blocks; per block it reads the column index,
+// the three entries (alpha, 0..2) from their planes and the three vector
+// entries at the column.  No cross-lane reduction is needed.  `xs` is
+// indexed by vector entry minus `xoff`.
+template <typename C, bool kShared>
+__device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t stride, const int* cols, int s0, int s1,
+                                           int al, const C* xs, int xoff) {
+    // cols: the row's column indices in shared memory, cols[s - s0]
+    using Tr = decltype(C{}.x);
+    Tr ar = 0, ai = 0, br = 0, bi = 0;
+    const C* v0 = val + (3 * al) * stride;
+    const C* v1 = v0 + stride;
+    const C* v2 = v1 + stride;
+    int s = s0;
+    for (; s + 1 < s1; s += 2) {  // two blocks per step, two accumulator pairs
+        const int xa = 3 * cols[s - s0] - xoff, xb = 3 * cols[s + 1 - s0] - xoff;
+        const C ma0 = ld_ro(v0 + s), ma1 = ld_ro(v1 + s), ma2 = ld_ro(v2 + s);
+        const C mb0 = ld_ro(v0 + s + 1), mb1 = ld_ro(v1 + s + 1), mb2 = ld_ro(v2 + s + 1);
+        const C xa0 = kShared ? xs[xa] : ld_cg(xs + xa), xa1 = kShared ? xs[xa + 1] : ld_cg(xs + xa + 1),
+                xa2 = kShared ? xs[xa + 2] : ld_cg(xs + xa + 2);
+        const C xb0 = kShared ? xs[xb] : ld_cg(xs + xb), xb1 = kShared ? xs[xb + 1] : ld_cg(xs + xb + 1),
+                xb2 = kShared ? xs[xb + 2] : ld_cg(xs + xb + 2);
+        ar += ma0.x * xa0.x - ma0.y * xa0.y + ma1.x * xa1.x - ma1.y * xa1.y + ma2.x * xa2.x - ma2.y * xa2.y;
+        ai += ma0.x * xa0.y + ma0.y * xa0.x + ma1.x * xa1.y + ma1.y * xa1.x + ma2.x * xa2.y + ma2.y * xa2.x;
+        br += mb0.x * xb0.x - mb0.y * xb0.y + mb1.x * xb1.x - mb1.y * xb1.y + mb2.x * xb2.x - mb2.y * xb2.y;
+        bi += mb0.x * xb0.y + mb0.y * xb0.x + mb1.x * xb1.y + mb1.y * xb1.x + mb2.x * xb2.y + mb2.y * xb2.x;
+    }
+    if (s < s1) {
+        const int xa = 3 * cols[s - s0] - xoff;
+        const C m0 = ld_ro(v0 + s), m1 = ld_ro(v1 + s), m2 = ld_ro(v2 + s);
+        const C x0 = kShared ? xs[xa] : ld_cg(xs + xa), x1 = kShared ? xs[xa + 1] : ld_cg(xs + xa + 1),
+                x2 = kShared ? xs[xa + 2] : ld_cg(xs + xa + 2);
+        ar += m0.x * x0.x - m0.y * x0.y + m1.x * x1.x - m1.y * x1.y + m2.x * x2.x - m2.y * x2.y;
+        ai += m0.x * x0.y + m0.y * x0.x + m1.x * x1.y + m1.y * x1.x + m2.x * x2.y + m2.y * x2.x;
+    }
+    return mk(ar + br, ai + bi);
+}
+
+// Copies the column indices of the warp's rows [rb, re) into shared memory
+// (one coalesced pass); returns the first block index sb of the range.
+__device__ __forceinline__ int stage_cols(const int* __restrict__ rp, const int* __restrict__ col, int rb, int re,
+                                          int* cols, int lane) {
+    const int sb = __ldg(rp + rb), se = __ldg(rp + re);
+    for (int j = lane; j < se - sb; j += 32) cols[j] = __ldg(col + sb + j);
+    __syncwarp();
+    return sb;
+}
+
+}  // namespace fe

@@ -24,8 +24,10 @@ namespace fe {
 
 constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
-constexpr int kMaxNV = 5;     // reduced values per column and barrier
+constexpr int kMaxNV = 11;    // reduced values per column and barrier
 constexpr int kTraceIters = 64;
+constexpr int kRowsPerWarpR1 = 10;   // R = 1 products: one thread per (row, component), 10 rows per warp
+constexpr int kColsPerWarp = 272;    // >= 10 rows x 27 blocks
 constexpr int kTracePhases = 8;
 
 struct SyncState {
@@ -35,11 +37,15 @@ struct SyncState {
     int pad;
 };
 
-// Inner-loop storage.  The recurrences (d, r, u, p, s) and all inner
-// products are FP64; the matrix, the preconditioner and the sparse product
-// run in the matrix precision TM (complex64 in the mixed mode), on a TM copy
-// uM of u.  The FP64 recurrences are what keeps the Krylov loop converging:
-// with complex64 recurrences the loop stalls on these indefinite systems.
+// Krylov storage.  The solution x, the recurrences (r, u, p, s) and all inner
+// products are FP64; the sparse product of the Krylov loop runs in the
+// matrix precision TM (complex64 in the mixed mode) on TM copies uM, pM of u
+// and p.  FP64 recurrences and an FP64 block-Jacobi application keep the
+// loop converging (with complex64 recurrences it stalls on these indefinite
+// systems); the complex64 product halves the matrix bytes and runs on the
+// FP32 pipes.  The FP64 true residual replaces the recursive one whenever the
+// latter has dropped by `reliable` since the last replacement (reliable
+// updates), so the Krylov directions are kept across refinements.
 struct SolveParams {
     int n_rows, n_cta;
     const int* rp;
@@ -47,25 +53,26 @@ struct SolveParams {
     const double2* val64;
     const void* valM;       // matrix in the inner precision
     int64_t stride;         // plane stride of the block values
-    const double2* dinv64;  // block-Jacobi inverse (FP64: the preconditioner is applied in FP64)
+    const double2* dinv64;  // block-Jacobi inverse, applied in FP64
     const double2* b;
     double2* x;
-    double2* r64;
-    double2* d;
     double2* r;
     double2* u;
     double2* p;
     double2* s;
-    void* uM;  // u rounded to the inner precision (aliases u when TM = double)
+    void* uM;  // u in the inner precision (aliases u when TM = double)
+    void* pM;  // p in the inner precision (aliases p when TM = double)
     void* w;   // w = A uM in the inner precision
     SyncState* sync;
     double* partial;
     double* result;
-    double tol, inner_tol;
+    double tol, reliable;
+    int restart;  // 1: a true-residual pass restarts the directions (p = s = 0); 0: keeps them
     int max_iter, max_outer, use_x0;
     int halo;       // bound on |column rank - row rank|
     int stage;      // stage the CTA's uM halo in shared memory (1) or gather from L2 (0)
     int red_bytes;  // dynamic shared memory used by the column sums
+    int col_bytes;  // dynamic shared memory for the per-warp column-index staging (R = 1)
     int* rep_status;
     int* rep_iters;
     int* rep_outer;
@@ -217,7 +224,8 @@ __device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int
         mbar_expect_tx(mbar, (unsigned)(a1 - a0));
         bulk_g2s(halo_buf, (const char*)v + a0, (unsigned)(a1 - a0), mbar);
     }
-    bool ok = mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns);
+    // one decision for the whole CTA (no thread may leave while others wait at a barrier)
+    const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns)) != 0;
     if (!ok) {
         atomicCAS(&P.sync->err, 0, kDevTimeout);
         mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns);  // let the copy land before leaving
@@ -227,105 +235,122 @@ __device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int
     return ok;
 }
 
-// w = A uM over the CTA's rows (inner precision), with the per-column FP64
-// partial dot products g += r^T u, dl += u^T w, rr += |r|^2 (own rows).
+// One Krylov product phase over the CTA's rows: w = A uM and, for columns
+// whose s must be refreshed after a residual replacement, s = A pM; with the
+// per-column FP64 partial dots
+//   acc[0..1] = r^T u, acc[2..3] = u^T w, acc[4] = |r|^2,
+//   acc[5..6] = u^T s, acc[7..8] = p^T w, acc[9..10] = p^T s (refresh only).
 template <typename TM, int R, bool kStaged>
-__device__ __forceinline__ void spmv_dots(const SolveParams& P, const typename CplxT<TM>::type* xs, int xshift,
-                                          int r0, int r1, double (&acc)[5]) {
+__device__ __forceinline__ bool product_phase(const SolveParams& P, const typename CplxT<TM>::type* xs, int xshift,
+                                              int r0, int r1, const int* s_refresh, bool any_refresh, int* s_cols,
+                                              double (&acc)[11]) {
+    bool ok = true;
     using C = typename CplxT<TM>::type;
     const C* valM = (const C*)P.valM;
     const C* uM = (const C*)P.uM;
+    const C* pM = (const C*)P.pM;
     C* w = (C*)P.w;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    if (R == 1) {
-        int row = r0 + warp;
-        int s0 = 0, s1 = 1, mycol = 0;
-        if (row < r1) {
-            s0 = __ldg(P.rp + row);
-            s1 = __ldg(P.rp + row + 1);
-            mycol = __ldg(P.col + s0 + min(lane, s1 - s0 - 1));
+    auto dots = [&](size_t o, const C& wy, bool refresh, const C& sy) {
+        const double2 rv = __ldcg(P.r + o), uv = __ldcg(P.u + o), wd = to_c128(wy);
+        acc[0] += rv.x * uv.x - rv.y * uv.y;
+        acc[1] += rv.x * uv.y + rv.y * uv.x;
+        acc[2] += uv.x * wd.x - uv.y * wd.y;
+        acc[3] += uv.x * wd.y + uv.y * wd.x;
+        acc[4] += rv.x * rv.x + rv.y * rv.y;
+        if (refresh) {
+            const double2 pv = __ldcg(P.p + o), sd = to_c128(sy);
+            acc[5] += uv.x * sd.x - uv.y * sd.y;
+            acc[6] += uv.x * sd.y + uv.y * sd.x;
+            acc[7] += pv.x * wd.x - pv.y * wd.y;
+            acc[8] += pv.x * wd.y + pv.y * wd.x;
+            acc[9] += pv.x * sd.x - pv.y * sd.y;
+            acc[10] += pv.x * sd.y + pv.y * sd.x;
+            P.s[o] = sd;
         }
-        for (; row < r1; row += kWarps) {
-            // prefetch the next row's extent and column indices
-            const int nrow = row + kWarps;
-            int ns0 = 0, ns1 = 1, ncol = 0;
-            if (nrow < r1) {
-                ns0 = __ldg(P.rp + nrow);
-                ns1 = __ldg(P.rp + nrow + 1);
-                ncol = __ldg(P.col + ns0 + min(lane, ns1 - ns0 - 1));
-            }
-            const int o = 3 * row + (lane < 3 ? lane : 0);
-            const double2 rv = __ldcg(P.r + o);  // issued early, consumed after the product
-            const double2 uv = __ldcg(P.u + o);
-            C y0, y1, y2;
-            row_product_r1x<C, kStaged>(valM, P.stride, mycol, s0, s1, kStaged ? xs : uM, kStaged ? -xshift : 0, lane, y0, y1,
-                                        y2);
-            if (lane < 3) {
-                const C y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
+    };
+    if (R == 1) {
+        // one thread per (row, component): ten rows per warp, their column
+        // indices staged in shared memory first
+        int* cols = s_cols + warp * kColsPerWarp;
+        const bool refresh = s_refresh[0] != 0;
+        const int al = lane % 3;
+        for (int rb = r0 + warp * kRowsPerWarpR1; rb < r1; rb += kWarps * kRowsPerWarpR1) {
+            const int re = min(rb + kRowsPerWarpR1, r1);
+            const int sb = stage_cols(P.rp, P.col, rb, re, cols, lane);
+            const int row = rb + lane / 3;
+            if (lane < 30 && row < re) {
+                const int s0 = __ldg(P.rp + row), s1 = __ldg(P.rp + row + 1);
+                const int* rc = cols + (s0 - sb);
+                const C y = row_component<C, kStaged>(valM, P.stride, rc, s0, s1, al, kStaged ? xs : uM,
+                                                      kStaged ? -xshift : 0);
+                const size_t o = (size_t)3 * row + al;
                 w[o] = y;
-                const double2 yd = to_c128(y);
-                acc[0] += rv.x * uv.x - rv.y * uv.y;
-                acc[1] += rv.x * uv.y + rv.y * uv.x;
-                acc[2] += uv.x * yd.x - uv.y * yd.y;
-                acc[3] += uv.x * yd.y + uv.y * yd.x;
-                acc[4] += rv.x * rv.x + rv.y * rv.y;
+                C sy = y;
+                if (refresh) sy = row_component<C, false>(valM, P.stride, rc, s0, s1, al, pM, 0);
+                dots(o, y, refresh, sy);
             }
-            s0 = ns0;
-            s1 = ns1;
-            mycol = ncol;
+            __syncwarp();
         }
     } else {
         constexpr int kRowsPerWarp = 32 / R;
         const int c = lane % R;
+        const bool refresh = s_refresh[c] != 0;
         for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1; row += kWarps * kRowsPerWarp) {
-            double2 rv[3], uv[3];
+            const int s0 = __ldg(P.rp + row), s1 = __ldg(P.rp + row + 1);
+            C y[3], sy[3];
+            row_product_colx<C, kStaged>(valM, P.stride, P.col, s0, s1, kStaged ? xs : uM, kStaged ? -xshift : 0, R,
+                                         c, y[0], y[1], y[2]);
+            if (refresh) row_product_colx<C, false>(valM, P.stride, P.col, s0, s1, pM, 0, R, c, sy[0], sy[1], sy[2]);
 #pragma unroll
             for (int al = 0; al < 3; ++al) {
-                rv[al] = __ldcg(P.r + (size_t)(3 * row + al) * R + c);
-                uv[al] = __ldcg(P.u + (size_t)(3 * row + al) * R + c);
-            }
-            C y[3];
-            row_product_colx<C, kStaged>(valM, P.stride, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), kStaged ? xs : uM,
-                                         kStaged ? -xshift : 0, R, c, y[0], y[1], y[2]);
-#pragma unroll
-            for (int al = 0; al < 3; ++al) {
-                w[(size_t)(3 * row + al) * R + c] = y[al];
-                const double2 yd = to_c128(y[al]);
-                acc[0] += rv[al].x * uv[al].x - rv[al].y * uv[al].y;
-                acc[1] += rv[al].x * uv[al].y + rv[al].y * uv[al].x;
-                acc[2] += uv[al].x * yd.x - uv[al].y * yd.y;
-                acc[3] += uv[al].x * yd.y + uv[al].y * yd.x;
-                acc[4] += rv[al].x * rv[al].x + rv[al].y * rv[al].y;
+                const size_t o = (size_t)(3 * row + al) * R + c;
+                w[o] = y[al];
+                dots(o, y[al], refresh, refresh ? sy[al] : y[al]);
             }
         }
     }
+    (void)any_refresh;
+    return ok;
 }
 
 #define FE_TRACE_MARK(k)                                                                        \
     do {                                                                                        \
-        if (P.trace && tid == 0 && trace_it < kTraceIters)                                      \
-            P.trace[((size_t)blockIdx.x * kTraceIters + trace_it) * kTracePhases + (k)] = globaltimer_ns(); \
+        if (P.trace && tid == 0 && trace_it < kTraceIters && blockIdx.x == gridDim.x / 2)       \
+            P.trace[((size_t)trace_it) * kTracePhases + (k)] = globaltimer_ns();                 \
     } while (0)
 
-// The persistent solve: FP64 true residual, inner preconditioned COCG in the
-// single-reduction form of Chronopoulos and Gear (one sparse product w = A u
-// and one fused reduction of r^T u, u^T w, ||r||^2 per iteration; two grid
-// barriers), FP64 solution update.
+// The persistent solve of A X = B for R right-hand sides.
+//   [R] replacement: r = b - A x in FP64 for the columns that ask for it
+//       (all at the start), norms, convergence test on the true residual;
+//       then u = Dinv r and the inner-precision copies.
+//   [A] product: w = A uM (s = A pM after a replacement), fused dots.
+//   [B] scalars of the single-reduction COCG (Chronopoulos and Gear); after
+//       a replacement the denominator p^T A p is expanded exactly from the
+//       refreshed products instead of the recurrence.
+//   [C] update: p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s,
+//       u = Dinv r (one thread per dof, node components exchanged in shared
+//       memory).
+// Grid barriers separate the phases; [A] and [R] end in fused reductions.
 template <typename TM, int R>
 __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
     using C = typename CplxT<TM>::type;
     C* uM = (C*)P.uM;
+    C* pM = (C*)P.pM;
     const C* wv = (const C*)P.w;
+    constexpr bool kSplit = sizeof(C) != sizeof(double2);  // inner copies are separate buffers
 
     extern __shared__ __align__(128) char dyn[];
     double* s_red = (double*)dyn;
-    char* halo_buf = dyn + P.red_bytes;
+    int* s_cols = (int*)(dyn + P.red_bytes);
+    char* halo_buf = dyn + P.red_bytes + P.col_bytes;
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ double s_in[kMaxNV * R], s_out[kMaxNV * R];
-    __shared__ double s_rn[R], s_itol[R], s_rel[R];
+    __shared__ double s_bn[R], s_rr_ref[R], s_rel[R];
     __shared__ double s_gam_r[R], s_gam_i[R], s_al_r[R], s_al_i[R], s_be_r[R], s_be_i[R];
-    __shared__ int s_active[R], s_pass[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_pass_it[R];
-    __shared__ int s_any;
+    __shared__ int s_active[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_first[R], s_refresh[R],
+        s_repl[R];
+    __shared__ int s_any_repl, s_any_active, s_any_refresh;
     __shared__ double2 s_exch[kThreads];
 
     const int tid = threadIdx.x;
@@ -333,6 +358,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
     const int r1 = (int)((int64_t)(blockIdx.x + 1) * P.n_rows / P.n_cta);
     const int n_items = (r1 - r0) * R;  // (node, column) pairs owned by this CTA
     const int my_c = tid % R;           // column of every item this thread handles
+    const size_t base_o = (size_t)3 * r0 * R;
     unsigned mbar_phase = 0;
     int trace_it = 0;
 
@@ -343,268 +369,324 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
         s_iters[tid] = 0;
         s_outer[tid] = 0;
         s_active[tid] = 0;
-        s_pass[tid] = 0;
+        s_first[tid] = 1;
+        s_refresh[tid] = 0;
+        s_repl[tid] = 1;  // the first pass computes the initial residual
         s_rel[tid] = 0.0;
+        s_bn[tid] = 0.0;
     }
-    if (!P.use_x0)
-        for (int i = tid; i < 3 * n_items; i += kThreads) P.x[(size_t)3 * r0 * R + i] = make_double2(0.0, 0.0);
+    for (int i = tid; i < 3 * n_items; i += kThreads) {
+        if (!P.use_x0) P.x[base_o + i] = make_double2(0.0, 0.0);
+        P.p[base_o + i] = make_double2(0.0, 0.0);
+        P.s[base_o + i] = make_double2(0.0, 0.0);
+    }
+    if (tid == 0) s_any_repl = 1;
     __syncthreads();
     if (!grid_reduce<0>(P, s_in, s_out)) goto out;
 
     for (;;) {
-        // ---- FP64 true residual r = b - A x and the norms ||r||, ||b|| ----
-        {
-            double acc[2] = {0.0, 0.0};
-            const int lane = tid & 31, warp = tid >> 5;
-            if (R == 1) {
-                int row = r0 + warp;
-                int s0 = 0, s1 = 1, mycol = 0;
-                if (row < r1) {
-                    s0 = __ldg(P.rp + row);
-                    s1 = __ldg(P.rp + row + 1);
-                    mycol = __ldg(P.col + s0 + min(lane, s1 - s0 - 1));
-                }
-                for (; row < r1; row += kWarps) {
-                    const int nrow = row + kWarps;
-                    int ns0 = 0, ns1 = 1, ncol = 0;
-                    if (nrow < r1) {
-                        ns0 = __ldg(P.rp + nrow);
-                        ns1 = __ldg(P.rp + nrow + 1);
-                        ncol = __ldg(P.col + ns0 + min(lane, ns1 - ns0 - 1));
-                    }
-                    const int o = 3 * row + (lane < 3 ? lane : 0);
-                    const double2 bv = __ldg(P.b + o);
-                    double2 y0, y1, y2;
-                    row_product_r1x<double2, false>(P.val64, P.stride, mycol, s0, s1, P.x, 0, lane, y0, y1, y2);
-                    if (lane < 3) {
-                        const double2 y = lane == 0 ? y0 : (lane == 1 ? y1 : y2);
-                        const double2 rv = make_double2(bv.x - y.x, bv.y - y.y);
-                        P.r64[o] = rv;
-                        acc[0] += rv.x * rv.x + rv.y * rv.y;
-                        acc[1] += bv.x * bv.x + bv.y * bv.y;
-                    }
-                    s0 = ns0;
-                    s1 = ns1;
-                    mycol = ncol;
-                }
-            } else {
-                constexpr int kRowsPerWarp = 32 / R;
-                const int c = lane % R;
-                for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1; row += kWarps * kRowsPerWarp) {
-                    double2 y[3];
-                    row_product_colx<double2, false>(P.val64, P.stride, P.col, __ldg(P.rp + row), __ldg(P.rp + row + 1), P.x,
-                                                     0, R, c, y[0], y[1], y[2]);
-#pragma unroll
-                    for (int al = 0; al < 3; ++al) {
-                        const size_t o = (size_t)(3 * row + al) * R + c;
-                        const double2 bv = __ldg(P.b + o);
-                        const double2 rv = make_double2(bv.x - y[al].x, bv.y - y[al].y);
-                        P.r64[o] = rv;
-                        acc[0] += rv.x * rv.x + rv.y * rv.y;
-                        acc[1] += bv.x * bv.x + bv.y * bv.y;
-                    }
-                }
-            }
-            cta_colsum<R, 2>(acc, s_red, s_in);
-            if (!grid_reduce<2 * R>(P, s_in, s_out)) goto out;
-        }
-        if (tid < R) {
-            const int c = tid;
-            const double rn = sqrt(s_out[c]), bn = sqrt(s_out[R + c]);
-            s_pass[c] = 0;
-            s_active[c] = 0;
-            if (!s_done[c]) {
-                const double rel = bn > 0.0 ? rn / bn : 0.0;
-                s_rel[c] = rel;
-                if (!(rel == rel)) {
-                    s_done[c] = 1;
-                    s_status[c] = FE_ERR_NOT_CONVERGED;
-                } else if (rel <= P.tol) {
-                    s_done[c] = 1;
-                    s_status[c] = FE_OK;
-                } else if (s_outer[c] >= P.max_outer || s_iters[c] >= P.max_iter || s_status[c] == FE_ERR_BREAKDOWN) {
-                    s_done[c] = 1;
-                    if (s_status[c] == FE_OK) s_status[c] = FE_ERR_NOT_CONVERGED;
-                } else {
-                    s_active[c] = 1;
-                    s_pass[c] = 1;
-                    s_pass_it[c] = 0;
-                    s_rn[c] = rn;
-                    s_itol[c] = fmax(P.inner_tol, 0.5 * P.tol * bn / rn);
-                    s_outer[c] += 1;
-                }
-            }
-        }
-        __syncthreads();
-        if (tid == 0) {
-            int any = 0;
-            for (int c = 0; c < R; ++c) any |= s_active[c];
-            s_any = any;
-        }
-        __syncthreads();
-        if (!s_any) break;
-
-        // ---- inner start: r = r64 / ||r64||, u = Dinv r, d = p = s = 0 ----
-        {
-            const bool act = s_active[my_c];
-            const double sc = act ? 1.0 / s_rn[my_c] : 0.0;
-            for (int i = tid; i < n_items; i += kThreads) {
-                const int node = r0 + i / R;
-                double2 rv[3], uv[3];
-#pragma unroll
-                for (int al = 0; al < 3; ++al) {
-                    const double2 w = __ldcg(P.r64 + (size_t)(3 * node + al) * R + my_c);
-                    rv[al] = make_double2(w.x * sc, w.y * sc);
-                }
-                apply_dinv(P.dinv64, node, rv, uv);
-#pragma unroll
-                for (int al = 0; al < 3; ++al) {
-                    const size_t o = (size_t)(3 * node + al) * R + my_c;
-                    P.r[o] = rv[al];
-                    P.u[o] = uv[al];
-                    if (sizeof(C) != sizeof(double2)) uM[o] = from_c128<C>(uv[al]);
-                    P.d[o] = make_double2(0.0, 0.0);
-                    P.p[o] = make_double2(0.0, 0.0);
-                    P.s[o] = make_double2(0.0, 0.0);
-                }
-            }
-            if (!grid_reduce<0>(P, s_in, s_out)) goto out;
-        }
-
-        // ---- inner iterations ----
-        for (bool first = true;; first = false) {
-            FE_TRACE_MARK(0);
-            // w = A u, gamma = r^T u, delta = u^T w, ||r||^2
+        if (s_any_repl) {
+            // ---- [R] FP64 true residual for the columns that ask for it ----
             {
-                double acc[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
-                if (P.stage) {
-                    int shift = 0;
-                    if (!stage_halo<C, R>(P, uM, r0, r1, halo_buf, &s_mbar, mbar_phase, shift)) goto out;
-                    FE_TRACE_MARK(1);
-                    spmv_dots<TM, R, true>(P, (const C*)halo_buf, shift, r0, r1, acc);
+                double acc[2] = {0.0, 0.0};
+                const int lane = tid & 31, warp = tid >> 5;
+                if (R == 1) {
+                    if (s_repl[0]) {
+                        int* cols = s_cols + warp * kColsPerWarp;
+                        const int al = lane % 3;
+                        for (int rb = r0 + warp * kRowsPerWarpR1; rb < r1; rb += kWarps * kRowsPerWarpR1) {
+                            const int re = min(rb + kRowsPerWarpR1, r1);
+                            const int sb = stage_cols(P.rp, P.col, rb, re, cols, lane);
+                            const int row = rb + lane / 3;
+                            if (lane < 30 && row < re) {
+                                const int s0 = __ldg(P.rp + row), s1 = __ldg(P.rp + row + 1);
+                                const size_t o = (size_t)3 * row + al;
+                                const double2 bv = __ldg(P.b + o);
+                                const double2 y = row_component<double2, false>(P.val64, P.stride, cols + (s0 - sb),
+                                                                                s0, s1, al, P.x, 0);
+                                const double2 rv = make_double2(bv.x - y.x, bv.y - y.y);
+                                P.r[o] = rv;
+                                acc[0] += rv.x * rv.x + rv.y * rv.y;
+                                acc[1] += bv.x * bv.x + bv.y * bv.y;
+                            }
+                            __syncwarp();
+                        }
+                    }
                 } else {
-                    spmv_dots<TM, R, false>(P, nullptr, 0, r0, r1, acc);
+                    constexpr int kRowsPerWarp = 32 / R;
+                    const int c = lane % R;
+                    if (s_repl[c]) {
+                        for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1;
+                             row += kWarps * kRowsPerWarp) {
+                            double2 y[3];
+                            row_product_colx<double2, false>(P.val64, P.stride, P.col, __ldg(P.rp + row),
+                                                             __ldg(P.rp + row + 1), P.x, 0, R, c, y[0], y[1], y[2]);
+#pragma unroll
+                            for (int al = 0; al < 3; ++al) {
+                                const size_t o = (size_t)(3 * row + al) * R + c;
+                                const double2 bv = __ldg(P.b + o);
+                                const double2 rv = make_double2(bv.x - y[al].x, bv.y - y[al].y);
+                                P.r[o] = rv;
+                                acc[0] += rv.x * rv.x + rv.y * rv.y;
+                                acc[1] += bv.x * bv.x + bv.y * bv.y;
+                            }
+                        }
+                    }
                 }
-                FE_TRACE_MARK(2);
-                cta_colsum<R, 5>(acc, s_red, s_in);
-                FE_TRACE_MARK(3);
-                if (!grid_reduce<5 * R>(P, s_in, s_out)) goto out;
-                FE_TRACE_MARK(4);
+                cta_colsum<R, 2>(acc, s_red, s_in);
+                if (!grid_reduce<2 * R>(P, s_in, s_out)) goto out;
             }
             if (tid < R) {
                 const int c = tid;
-                if (s_active[c]) {
-                    const double gr = s_out[c], gi = s_out[R + c];
-                    const double dr = s_out[2 * R + c], di = s_out[3 * R + c];
-                    const double nr2 = s_out[4 * R + c];  // ||r||^2
-                    if (!first) {
-                        s_iters[c] += 1;
-                        s_pass_it[c] += 1;
-                    }
-                    if (!(nr2 == nr2) || nr2 <= s_itol[c] * s_itol[c] || s_iters[c] >= P.max_iter || nr2 > 1e24) {
-                        s_active[c] = 0;
+                if (s_repl[c] && !s_done[c]) {
+                    if (s_first[c] && s_outer[c] == 0) s_bn[c] = sqrt(s_out[R + c]);
+                    const double rn = sqrt(s_out[c]), bn = s_bn[c];
+                    const double rel = bn > 0.0 ? rn / bn : 0.0;
+                    s_rel[c] = rel;
+                    s_outer[c] += 1;
+                    s_active[c] = 0;
+                    if (!(rel == rel)) {
+                        s_done[c] = 1;
+                        s_status[c] = FE_ERR_NOT_CONVERGED;
+                    } else if (rel <= P.tol) {
+                        s_done[c] = 1;
+                        s_status[c] = FE_OK;
+                    } else if (s_iters[c] >= P.max_iter || s_outer[c] > P.max_outer) {
+                        s_done[c] = 1;
+                        s_status[c] = FE_ERR_NOT_CONVERGED;
                     } else {
-                        double br = 0.0, bi = 0.0, er = dr, ei = di;
-                        if (!first) {
-                            // beta = gamma' / gamma;  denominator delta' - beta gamma' / alpha
-                            const double ig = rcp64(s_gam_r[c] * s_gam_r[c] + s_gam_i[c] * s_gam_i[c]);
-                            br = (gr * s_gam_r[c] + gi * s_gam_i[c]) * ig;
-                            bi = (gi * s_gam_r[c] - gr * s_gam_i[c]) * ig;
-                            const double tr = br * gr - bi * gi, ti = br * gi + bi * gr;  // beta gamma'
-                            const double ia = rcp64(s_al_r[c] * s_al_r[c] + s_al_i[c] * s_al_i[c]);
-                            er = dr - (tr * s_al_r[c] + ti * s_al_i[c]) * ia;  // delta' - beta gamma' / alpha
-                            ei = di - (ti * s_al_r[c] - tr * s_al_i[c]) * ia;
-                        }
-                        const double ed = er * er + ei * ei;
-                        const double gg = gr * gr + gi * gi;
-                        if (!(ed > 0.0) || !(ed < 1e300) || !(gg > 0.0)) {
-                            s_active[c] = 0;
-                            if (s_pass_it[c] == 0) s_status[c] = FE_ERR_BREAKDOWN;
-                        } else {
-                            const double ie = rcp64(ed);
-                            s_al_r[c] = (gr * er + gi * ei) * ie;
-                            s_al_i[c] = (gi * er - gr * ei) * ie;
-                            s_be_r[c] = br;
-                            s_be_i[c] = bi;
-                            s_gam_r[c] = gr;
-                            s_gam_i[c] = gi;
-                        }
+                        s_active[c] = 1;
+                        s_rr_ref[c] = rn * rn;
+                        s_refresh[c] = s_first[c] ? 0 : 1;
                     }
+                } else if (s_repl[c]) {
+                    s_active[c] = 0;
                 }
             }
             __syncthreads();
-            if (tid == 0) {
-                int any = 0;
-                for (int c = 0; c < R; ++c) any |= s_active[c];
-                s_any = any;
-            }
-            __syncthreads();
-            if (!s_any) break;
-            FE_TRACE_MARK(5);
-            // p = u + beta p; s = w + beta s; d += alpha p; r -= alpha s; u -= alpha Dinv s.
-            // One thread per (dof, column): item i of the CTA is vector entry
-            // 3*r0*R + i; a chunk holds whole nodes, so the three components of
-            // s a node's block-Jacobi product needs are exchanged in shared
-            // memory.
+            // u = Dinv r and the inner-precision copies for the replaced columns
             {
-                const bool act = s_active[my_c] != 0;
-                const double2 alpha = make_double2(s_al_r[my_c], s_al_i[my_c]);
-                const double2 nalpha = make_double2(-s_al_r[my_c], -s_al_i[my_c]);
-                const double2 beta = make_double2(s_be_r[my_c], s_be_i[my_c]);
                 constexpr int kChunk = (kThreads / (3 * R)) * (3 * R);
+                const bool act = s_repl[my_c] && s_active[my_c];
                 const int n3 = 3 * n_items;
                 for (int base = 0; base < n3; base += kChunk) {
                     const int i = base + tid;
                     const bool valid = act && tid < kChunk && i < n3;
-                    const size_t o = (size_t)3 * r0 * R + i;
-                    double2 ss = make_double2(0.0, 0.0);
+                    const size_t o = base_o + i;
+                    double2 rv = make_double2(0.0, 0.0);
                     if (valid) {
-                        const double2 pp = cfma(beta, __ldcg(P.p + o), __ldcg(P.u + o));
-                        ss = cfma(beta, __ldcg(P.s + o), to_c128(ld_cg(wv + o)));
-                        P.p[o] = pp;
-                        P.s[o] = ss;
-                        P.d[o] = cfma(alpha, pp, __ldcg(P.d + o));
-                        P.r[o] = cfma(nalpha, ss, __ldcg(P.r + o));
+                        rv = __ldcg(P.r + o);
+                        if (kSplit) pM[o] = from_c128<C>(__ldcg(P.p + o));
                     }
-                    s_exch[tid] = ss;
+                    s_exch[tid] = rv;
                     __syncthreads();
                     if (valid) {
                         const int node = r0 + i / (3 * R);
                         const int al = (i / R) % 3;
                         const double2* drow = P.dinv64 + (size_t)node * 9 + 3 * al;
-                        double2 q = make_double2(0.0, 0.0);
+                        double2 uu = make_double2(0.0, 0.0);
 #pragma unroll
-                        for (int be = 0; be < 3; ++be) q = cfma(__ldg(drow + be), s_exch[tid + (be - al) * R], q);
-                        const double2 uu = cfma(nalpha, q, __ldcg(P.u + o));
+                        for (int be = 0; be < 3; ++be) uu = cfma(__ldg(drow + be), s_exch[tid + (be - al) * R], uu);
                         P.u[o] = uu;
-                        if (sizeof(C) != sizeof(double2)) uM[o] = from_c128<C>(uu);
+                        if (kSplit) uM[o] = from_c128<C>(uu);
                     }
                     __syncthreads();
                 }
             }
-            FE_TRACE_MARK(6);
+            if (tid == 0) {
+                int any = 0, refr = 0;
+                for (int c = 0; c < R; ++c) {
+                    s_repl[c] = 0;
+                    any |= s_active[c];
+                    refr |= s_refresh[c];
+                }
+                s_any_active = any;
+                s_any_refresh = refr;
+                s_any_repl = 0;
+            }
             if (!grid_reduce<0>(P, s_in, s_out)) goto out;
-            FE_TRACE_MARK(7);
-            ++trace_it;
+            {
+                int any = 0;
+                for (int c = 0; c < R; ++c) any |= !s_done[c];
+                if (!any) break;
+            }
         }
 
-        // ---- FP64 solution update x += ||r|| d ----
-        if (s_pass[my_c]) {
-            const double sc = s_rn[my_c];
-            for (int i = tid; i < n_items; i += kThreads) {
-                const int node = r0 + i / R;
-#pragma unroll
-                for (int al = 0; al < 3; ++al) {
-                    const size_t o = (size_t)(3 * node + al) * R + my_c;
-                    const double2 dv = __ldcg(P.d + o);
-                    double2 xv = P.x[o];
-                    xv.x += sc * dv.x;
-                    xv.y += sc * dv.y;
-                    P.x[o] = xv;
+        // ---- [A] products and fused dots ----
+        FE_TRACE_MARK(0);
+        {
+            double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            if (P.stage) {
+                int shift = 0;
+                if (!stage_halo<C, R>(P, uM, r0, r1, halo_buf, &s_mbar, mbar_phase, shift)) goto out;
+                FE_TRACE_MARK(1);
+                if (!product_phase<TM, R, true>(P, (const C*)halo_buf, shift, r0, r1, s_refresh, s_any_refresh, s_cols,
+                                                acc)) {
+                    if (tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
+                    goto out;
+                }
+            } else {
+                if (!product_phase<TM, R, false>(P, nullptr, 0, r0, r1, s_refresh, s_any_refresh, s_cols, acc)) {
+                    if (tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
+                    goto out;
+                }
+            }
+            FE_TRACE_MARK(2);
+            if (s_any_refresh) {
+                cta_colsum<R, 11>(acc, s_red, s_in);
+                if (!grid_reduce<11 * R>(P, s_in, s_out)) goto out;
+            } else {
+                double a5[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
+                cta_colsum<R, 5>(a5, s_red, s_in);
+                FE_TRACE_MARK(3);
+                if (!grid_reduce<5 * R>(P, s_in, s_out)) goto out;
+            }
+            FE_TRACE_MARK(4);
+        }
+        // ---- [B] scalars ----
+        // B1: does any column need its true residual first?  (No state of the
+        // other columns changes in a replacement round: they redo the same
+        // products next round.)
+        if (tid < R) {
+            const int c = tid;
+            if (s_active[c]) {
+                const double rr = s_out[4 * R + c];
+                const double tb = P.tol * s_bn[c];
+                const bool small = rr <= tb * tb || rr < P.reliable * P.reliable * s_rr_ref[c];
+                if (!(rr == rr) || s_iters[c] >= P.max_iter || (!s_first[c] && small)) {
+                    s_repl[c] = 1;
+                    if (P.restart) s_first[c] = 1;
                 }
             }
         }
+        __syncthreads();
+        if (tid == 0) {
+            int any_repl = 0;
+            for (int c = 0; c < R; ++c) any_repl |= s_repl[c];
+            s_any_repl = any_repl;
+        }
+        __syncthreads();
+        if (s_any_repl) {
+            for (int i = tid; i < 3 * n_items; i += kThreads) {
+                const int c = i % R;
+                if (s_repl[c] && s_first[c]) {
+                    P.p[base_o + i] = make_double2(0.0, 0.0);
+                    P.s[base_o + i] = make_double2(0.0, 0.0);
+                }
+            }
+            continue;
+        }
+        // B2: Chronopoulos-Gear scalars (exact p^T A p after a replacement)
+        if (tid < R) {
+            const int c = tid;
+            if (s_active[c]) {
+                const double gr = s_out[c], gi = s_out[R + c];
+                const double dr = s_out[2 * R + c], di = s_out[3 * R + c];
+                double br = 0.0, bi = 0.0, er = dr, ei = di;
+                if (!s_first[c]) {
+                    // beta = gamma / gamma_old
+                    const double ig = rcp64(s_gam_r[c] * s_gam_r[c] + s_gam_i[c] * s_gam_i[c]);
+                    br = (gr * s_gam_r[c] + gi * s_gam_i[c]) * ig;
+                    bi = (gi * s_gam_r[c] - gr * s_gam_i[c]) * ig;
+                    if (s_refresh[c]) {
+                        // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
+                        const double e12r = s_out[5 * R + c] + s_out[7 * R + c];
+                        const double e12i = s_out[6 * R + c] + s_out[8 * R + c];
+                        const double e3r = s_out[9 * R + c], e3i = s_out[10 * R + c];
+                        const double b2r = br * br - bi * bi, b2i = 2.0 * br * bi;
+                        er = dr + (br * e12r - bi * e12i) + (b2r * e3r - b2i * e3i);
+                        ei = di + (br * e12i + bi * e12r) + (b2r * e3i + b2i * e3r);
+                    } else {
+                        // delta - beta gamma / alpha_old
+                        const double tr = br * gr - bi * gi, ti = br * gi + bi * gr;
+                        const double ia = rcp64(s_al_r[c] * s_al_r[c] + s_al_i[c] * s_al_i[c]);
+                        er = dr - (tr * s_al_r[c] + ti * s_al_i[c]) * ia;
+                        ei = di - (ti * s_al_r[c] - tr * s_al_i[c]) * ia;
+                    }
+                }
+                const double ed = er * er + ei * ei;
+                const double gg = gr * gr + gi * gi;
+                if (!(ed > 0.0) || !(ed < 1e300) || !(gg > 0.0)) {
+                    if (s_first[c]) {  // breakdown right after a (re)start
+                        s_active[c] = 0;
+                        s_done[c] = 1;
+                        s_status[c] = FE_ERR_BREAKDOWN;
+                    } else {  // restart from the true residual next round
+                        s_repl[c] = 1;
+                        s_first[c] = 1;
+                    }
+                } else {
+                    const double ie = rcp64(ed);
+                    s_al_r[c] = (gr * er + gi * ei) * ie;
+                    s_al_i[c] = (gi * er - gr * ei) * ie;
+                    s_be_r[c] = br;
+                    s_be_i[c] = bi;
+                    s_gam_r[c] = gr;
+                    s_gam_i[c] = gi;
+                    s_iters[c] += 1;
+                    s_first[c] = 0;
+                    s_refresh[c] = 0;
+                }
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            int any_repl = 0, refr = 0;
+            for (int c = 0; c < R; ++c) {
+                any_repl |= s_repl[c];
+                refr |= s_refresh[c];
+            }
+            s_any_repl = any_repl;  // a breakdown restarts at the top of the next round
+            s_any_refresh = refr;
+        }
+        __syncthreads();
+        FE_TRACE_MARK(5);
+        // ---- [C] update, one thread per (dof, column) ----
+        {
+            const bool act = s_active[my_c] != 0 && !s_repl[my_c];
+            if (s_active[my_c] && s_repl[my_c])
+                for (int i = tid; i < 3 * n_items; i += kThreads) {
+                    P.p[base_o + i] = make_double2(0.0, 0.0);
+                    P.s[base_o + i] = make_double2(0.0, 0.0);
+                }
+            const double2 alpha = make_double2(s_al_r[my_c], s_al_i[my_c]);
+            const double2 nalpha = make_double2(-s_al_r[my_c], -s_al_i[my_c]);
+            const double2 beta = make_double2(s_be_r[my_c], s_be_i[my_c]);
+            constexpr int kChunk = (kThreads / (3 * R)) * (3 * R);
+            const int n3 = 3 * n_items;
+            for (int base = 0; base < n3; base += kChunk) {
+                const int i = base + tid;
+                const bool valid = act && tid < kChunk && i < n3;
+                const size_t o = base_o + i;
+                double2 rn = make_double2(0.0, 0.0);
+                if (valid) {
+                    const double2 pp = cfma(beta, __ldcg(P.p + o), __ldcg(P.u + o));
+                    const double2 ss = cfma(beta, __ldcg(P.s + o), to_c128(ld_cg(wv + o)));
+                    P.p[o] = pp;
+                    P.s[o] = ss;
+                    P.x[o] = cfma(alpha, pp, __ldcg(P.x + o));
+                    rn = cfma(nalpha, ss, __ldcg(P.r + o));
+                    P.r[o] = rn;
+                }
+                s_exch[tid] = rn;
+                __syncthreads();
+                if (valid) {
+                    const int node = r0 + i / (3 * R);
+                    const int al = (i / R) % 3;
+                    const double2* drow = P.dinv64 + (size_t)node * 9 + 3 * al;
+                    double2 uu = make_double2(0.0, 0.0);
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) uu = cfma(__ldg(drow + be), s_exch[tid + (be - al) * R], uu);
+                    P.u[o] = uu;
+                    if (kSplit) uM[o] = from_c128<C>(uu);
+                }
+                __syncthreads();
+            }
+        }
+        FE_TRACE_MARK(6);
         if (!grid_reduce<0>(P, s_in, s_out)) goto out;
+        FE_TRACE_MARK(7);
+        ++trace_it;
     }
 out:
     if (blockIdx.x == 0 && tid < R) {
@@ -670,10 +752,10 @@ fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewav
                     DevBuf& wave_buf);
 
 struct Workspace {
-    DevBuf b, x, r64, d, r, u, p, s, uM, w, partial, result, sync, rep, trace;
+    DevBuf b, x, r, u, p, s, uM, pM, w, partial, result, sync, rep, trace;
 };
 
-constexpr size_t kSmemBudget = 200 * 1024;
+constexpr size_t kSmemBudget = 200 * 1024;  // dynamic; static shared memory adds ~20 KB
 
 template <typename T, int R>
 static fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
@@ -683,10 +765,11 @@ static fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
     // vector halo live in dynamic shared memory
     P.n_cta = std::min(ctx->num_sms, std::max(1, P.n_rows));
     P.red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
+    P.col_bytes = R == 1 ? (int)(kWarps * kColsPerWarp * sizeof(int)) : 0;
     const int64_t rows_per_cta = (P.n_rows + P.n_cta - 1) / P.n_cta + 1;
     const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
-    P.stage = (P.halo > 0 && (size_t)P.red_bytes + (size_t)halo_bytes <= kSmemBudget) ? 1 : 0;
-    const size_t dyn = (size_t)P.red_bytes + (P.stage ? (size_t)halo_bytes : 0);
+    P.stage = (P.halo > 0 && (size_t)P.red_bytes + P.col_bytes + (size_t)halo_bytes <= kSmemBudget) ? 1 : 0;
+    const size_t dyn = (size_t)P.red_bytes + P.col_bytes + (P.stage ? (size_t)halo_bytes : 0);
     FE_CUDA(cudaFuncSetAttribute((const void*)k_solve<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<T, R>, kThreads, dyn));
@@ -741,18 +824,18 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
     const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);  // inner-precision vectors (uM, w)
     Workspace w;
     auto cleanup = [&]() {
-        for (DevBuf* b : {&w.b, &w.x, &w.r64, &w.d, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.w, &w.partial, &w.result,
-                          &w.sync, &w.rep, &w.trace})
+        for (DevBuf* b : {&w.b, &w.x, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.pM, &w.w, &w.partial, &w.result, &w.sync,
+                          &w.rep, &w.trace})
             dev_free(st, *b);
     };
     fe_status e = FE_OK;
     const size_t nv = (size_t)n_dof * R;
     const int max_cta = 2 * ctx->num_sms;
     for (auto pr : {std::make_pair(&w.b, nv * sizeof(double2)), std::make_pair(&w.x, nv * sizeof(double2)),
-                    std::make_pair(&w.r64, nv * sizeof(double2)), std::make_pair(&w.d, nv * sizeof(double2)),
                     std::make_pair(&w.r, nv * sizeof(double2)), std::make_pair(&w.u, nv * sizeof(double2)),
                     std::make_pair(&w.p, nv * sizeof(double2)), std::make_pair(&w.s, nv * sizeof(double2)),
-                    std::make_pair(&w.uM, fp64 ? (size_t)16 : nv * esz), std::make_pair(&w.w, nv * esz),
+                    std::make_pair(&w.uM, fp64 ? (size_t)16 : nv * esz),
+                    std::make_pair(&w.pM, fp64 ? (size_t)16 : nv * esz), std::make_pair(&w.w, nv * esz),
                     std::make_pair(&w.partial, (size_t)max_cta * kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.result, (size_t)kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.sync, sizeof(SyncState)),
@@ -793,13 +876,12 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         P.dinv64 = (const double2*)s->dinv64.ptr;
         P.b = (const double2*)w.b.ptr;
         P.x = (double2*)w.x.ptr;
-        P.r64 = (double2*)w.r64.ptr;
-        P.d = (double2*)w.d.ptr;
         P.r = (double2*)w.r.ptr;
         P.u = (double2*)w.u.ptr;
         P.p = (double2*)w.p.ptr;
         P.s = (double2*)w.s.ptr;
         P.uM = fp64 ? w.u.ptr : w.uM.ptr;
+        P.pM = fp64 ? w.p.ptr : w.pM.ptr;
         P.w = w.w.ptr;
         P.trace = (unsigned long long*)w.trace.ptr;
         // lexicographic node ranks: a neighbour is at most one plane, one
@@ -809,7 +891,8 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         P.partial = (double*)w.partial.ptr;
         P.result = (double*)w.result.ptr;
         P.tol = o.tol;
-        P.inner_tol = fp64 ? 0.0 : o.inner_tol;
+        P.reliable = fp64 ? 0.0 : o.reliable;
+        P.restart = fp64 ? 0 : 1;
         P.max_iter = o.max_iter;
         P.max_outer = o.max_outer;
         P.use_x0 = use_x0 ? 1 : 0;
@@ -851,7 +934,7 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
                 sum[0] += (double)(b[0] - a[kTracePhases - 1]);
                 ++n_it;
             }
-            fprintf(stderr, "FE_TRACE cta0 %d iterations, ns per phase:", n_it);
+            fprintf(stderr, "FE_TRACE mid-cta %d iterations, ns per phase:", n_it);
             for (int k = 0; k < kTracePhases; ++k) fprintf(stderr, " %d:%.0f", k, n_it ? sum[k] / n_it : 0.0);
             fprintf(stderr, "\n");
         }
@@ -887,7 +970,7 @@ static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
         set_error("solve: precision must be FP64 or MIXED");
         return FE_ERR_INVALID_ARG;
     }
-    if (!(out.tol > 0.0) || out.max_iter < 1 || out.max_outer < 1 || out.inner_tol < 0.0 || out.rhs_tile < 0) {
+    if (!(out.tol > 0.0) || out.max_iter < 1 || out.max_outer < 1 || !(out.reliable >= 0.0 && out.reliable < 1.0) || out.rhs_tile < 0) {
         set_error("solve: bad tolerance or iteration limits");
         return FE_ERR_INVALID_ARG;
     }
@@ -904,9 +987,9 @@ void fe_solve_opts_default(fe_solve_opts* o) {
     if (!o) return;
     o->precision = FE_PREC_MIXED;
     o->tol = 1e-8;
-    o->inner_tol = 1e-4;
+    o->reliable = 1e-4;
     o->max_iter = 20000;
-    o->max_outer = 30;
+    o->max_outer = 200;
     o->rhs_tile = 0;
 }
 

@@ -60,7 +60,7 @@ class fe_planewave(C.Structure):
 
 
 class fe_solve_opts(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("inner_tol", C.c_double),
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32)]
 
 
@@ -291,11 +291,11 @@ def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
     _check(load().fe_spmv(ctx, system, int(precision), int(nrhs), _ptr(x), _ptr(y)), "fe_spmv")
 
 
-def solve_opts(precision=FE_PREC_MIXED, tol=1e-8, inner_tol=1e-4, max_iter=20000, max_outer=30,
+def solve_opts(precision=FE_PREC_MIXED, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
                rhs_tile=0) -> fe_solve_opts:
     o = fe_solve_opts()
     load().fe_solve_opts_default(C.byref(o))
-    o.precision, o.tol, o.inner_tol = int(precision), float(tol), float(inner_tol)
+    o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
     o.max_iter, o.max_outer, o.rhs_tile = int(max_iter), int(max_outer), int(rhs_tile)
     return o
 
