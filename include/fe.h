@@ -232,6 +232,32 @@ fe_status fe_solve_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void
                        const fe_solve_opts* o, void* x_out, int32_t x_on_device, int32_t use_x0,
                        fe_solve_report* rep);
 
+/* Solve without any allocation, for callers that cannot allocate device
+ * memory while they run (for example code already inside stream capture, a
+ * host thread that must not block on the allocator, or an embedding that owns
+ * every allocation of its process).  The paper has no counterpart.
+ *
+ * Same method and options as fe_solve_rhs, for a caller right-hand side in
+ * DEVICE memory: b_dev and x_dev are complex128 [n_dof][nrhs] device buffers
+ * (x_dev holds the initial guess when use_x0 = 1), nrhs one of 1, 2, 4, 8,
+ * 16, 32.  rep: optional host array of nrhs reports.
+ *
+ * Scratch: the call keeps all of its workspace in one file-scope device array
+ * of 32 MiB (every GPU that loads the library holds it until the process
+ * exits); it calls no cudaMalloc / cudaFree and no allocating routine.  The
+ * need is about 88 bytes per unknown and right-hand side (mixed precision;
+ * 80 in FP64) plus a few KiB, so n_dof * nrhs may reach roughly 380 000; a
+ * larger problem is rejected with FE_ERR_INVALID_ARG and a message naming the
+ * bytes it would need.  The first call on a device looks the array's device
+ * address up (once per device, with that device current); make that first
+ * call before any stream capture.  Every call uses the same array: two calls
+ * whose GPU work overlaps (two contexts or streams at once) race on it and
+ * corrupt each other's results.  The call returns after the solve has
+ * finished (it synchronises the context stream to read the reports).
+ * Errors: as fe_solve_rhs. */
+fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b_dev, void* x_dev,
+                               int32_t use_x0, const fe_solve_opts* o, fe_solve_report* rep);
+
 /* Device-side statistics of the most recent fe_solve_batch / fe_solve_rhs
  * call on this context, measured with CUDA events on the context stream
  * around the persistent solve launches. */

@@ -963,6 +963,40 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
     return worst;
 }
 
+// ---------------------------------------------------------------------------
+// Fixed scratch for callers that cannot allocate device memory.
+//
+// fe_solve_rhs_noalloc keeps its whole workspace (Krylov vectors, reduction
+// partials, barrier state, reports) in this file-scope device array instead
+// of allocating it per call.  Every GPU that loads the library holds the array
+// until the process exits.  Host code must not use `g_solve_scratch` as a
+// device address (it is a host-side stand-in); the address is looked up once
+// per device with cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB per device
+static __device__ __align__(256) unsigned char g_solve_scratch[kStaticScratchBytes];
+constexpr int kMaxDevices = 64;
+static void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+static fe_status static_scratch(int device, char** out) {
+    if (device < 0 || device >= kMaxDevices) {
+        set_error("fe_solve_rhs_noalloc: device %d outside 0..%d", device, kMaxDevices - 1);
+        return FE_ERR_INVALID_ARG;
+    }
+    if (!g_scratch_addr[device]) {
+        void* ptr = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&ptr, g_solve_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_error("fe_solve_rhs_noalloc: cudaGetSymbolAddress of the static scratch failed: %s",
+                      cudaGetErrorString(e));
+            return FE_ERR_CUDA;
+        }
+        g_scratch_addr[device] = ptr;
+    }
+    *out = (char*)g_scratch_addr[device];
+    return FE_OK;
+}
+
 static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
     fe_solve_opts_default(&out);
     if (o) out = *o;
@@ -1099,6 +1133,124 @@ fe_status fe_solve_batch(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const fe
     dev_free(st, wb);
     dev_free(st, hx);
     return e;
+}
+
+
+fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b_dev, void* x_dev,
+                               int32_t use_x0, const fe_solve_opts* o, fe_solve_report* rep) {
+    if (!ctx || !s || !b_dev || !x_dev) {
+        set_error("fe_solve_rhs_noalloc: NULL argument");
+        return FE_ERR_INVALID_ARG;
+    }
+    if (nrhs != 1 && nrhs != 2 && nrhs != 4 && nrhs != 8 && nrhs != 16 && nrhs != 32) {
+        set_error("fe_solve_rhs_noalloc: nrhs must be 1, 2, 4, 8, 16 or 32 (got %d)", nrhs);
+        return FE_ERR_INVALID_ARG;
+    }
+    fe_solve_opts opt;
+    FE_TRY(check_opts(o, opt));
+    const bool fp64 = opt.precision == FE_PREC_FP64;
+    if (!fp64 && !s->val32.ptr) {
+        set_error("fe_solve_rhs_noalloc: mixed-precision solve of a system assembled in FP64 only");
+        return FE_ERR_INVALID_ARG;
+    }
+    FE_CUDA(cudaSetDevice(ctx->device));
+    char* base = nullptr;
+    FE_TRY(static_scratch(ctx->device, &base));
+    const fe_mesh* m = s->mesh;
+    const int R = nrhs;
+    const size_t nv = (size_t)3 * m->n_act * R;
+    const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
+    const int max_cta = 2 * ctx->num_sms;
+    // carve the workspace, 256-byte aligned pieces
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        char* p = base + off;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    double2* r = (double2*)take(nv * sizeof(double2));
+    double2* u = (double2*)take(nv * sizeof(double2));
+    double2* pv = (double2*)take(nv * sizeof(double2));
+    double2* sv = (double2*)take(nv * sizeof(double2));
+    void* w = take(nv * esz);
+    void* uM = fp64 ? (void*)u : take(nv * esz);
+    void* pM = fp64 ? (void*)pv : take(nv * esz);
+    double* partial = (double*)take((size_t)max_cta * kMaxNV * R * sizeof(double));
+    double* result = (double*)take((size_t)kMaxNV * R * sizeof(double));
+    SyncState* sync = (SyncState*)take(sizeof(SyncState));
+    int* ri = (int*)take((size_t)3 * R * sizeof(int));
+    double* rrel = (double*)take((size_t)R * sizeof(double));
+    if (off > kStaticScratchBytes) {
+        set_error("fe_solve_rhs_noalloc: needs %zu bytes of scratch, the static array holds %zu (n_dof x nrhs too "
+                  "large)",
+                  off, kStaticScratchBytes);
+        return FE_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = ctx->stream;
+    FE_CUDA(cudaMemsetAsync(sync, 0, sizeof(SyncState), st));  // the array keeps the previous call's contents
+    SolveParams P{};
+    P.n_rows = m->n_act;
+    P.rp = (const int*)m->row_ptr.ptr;
+    P.col = (const int*)m->col_idx.ptr;
+    P.val64 = (const double2*)s->val64.ptr;
+    P.valM = fp64 ? s->val64.ptr : s->val32.ptr;
+    P.stride = s->stride;
+    P.dinv64 = (const double2*)s->dinv64.ptr;
+    P.b = (const double2*)b_dev;
+    P.x = (double2*)x_dev;
+    P.r = r;
+    P.u = u;
+    P.p = pv;
+    P.s = sv;
+    P.uM = uM;
+    P.pM = pM;
+    P.w = w;
+    P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
+    P.sync = sync;
+    P.partial = partial;
+    P.result = result;
+    P.tol = opt.tol;
+    P.reliable = fp64 ? 0.0 : opt.reliable;
+    P.restart = fp64 ? 0 : 1;
+    P.max_iter = opt.max_iter;
+    P.max_outer = opt.max_outer;
+    P.use_x0 = use_x0 ? 1 : 0;
+    P.rep_status = ri;
+    P.rep_iters = ri + R;
+    P.rep_outer = ri + 2 * R;
+    P.rep_rel = rrel;
+    P.trace = nullptr;
+    P.timeout_ns = 4000000000ull;
+    P.spin_ns = 0;
+    ctx->last_solve = fe_solve_stats{};
+    FE_TRY(fp64 ? dispatch<double>(ctx, R, P) : dispatch<float>(ctx, R, P));
+    SyncState hs{};
+    int h_ri[3 * 32];
+    double h_rel[32];
+    FE_CUDA(cudaMemcpyAsync(&hs, sync, sizeof(SyncState), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaMemcpyAsync(h_ri, ri, (size_t)3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaMemcpyAsync(h_rel, rrel, (size_t)R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last_solve.kernel_ms = ms;
+    if (hs.err) {
+        set_error("fe_solve_rhs_noalloc: a grid barrier wait expired (device status %d)", hs.err);
+        return FE_ERR_TIMEOUT;
+    }
+    fe_status worst = FE_OK;
+    for (int c = 0; c < R; ++c) {
+        if (rep) {
+            rep[c].status = h_ri[c];
+            rep[c].iterations = h_ri[R + c];
+            rep[c].outer = h_ri[2 * R + c];
+            rep[c].reserved = 0;
+            rep[c].rel_residual = h_rel[c];
+        }
+        ctx->last_solve.inner_iters += h_ri[R + c];
+        if (h_ri[c] != FE_OK && worst == FE_OK) worst = (fe_status)h_ri[c];
+    }
+    if (worst != FE_OK) set_error("fe_solve_rhs_noalloc: at least one right-hand side did not reach the tolerance");
+    return worst;
 }
 
 }  // extern "C"

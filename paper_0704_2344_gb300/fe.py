@@ -106,6 +106,8 @@ def load() -> C.CDLL:
         "fe_solve_rhs": (C.c_int, [P, P, C.c_int32, P, C.c_int32, C.POINTER(fe_solve_opts), P, C.c_int32,
                                    C.c_int32, C.POINTER(fe_solve_report)]),
         "fe_last_solve_stats": (C.c_int, [P, C.POINTER(fe_solve_stats)]),
+        "fe_solve_rhs_noalloc": (C.c_int, [P, P, C.c_int32, P, P, C.c_int32, C.POINTER(fe_solve_opts),
+                                           C.POINTER(fe_solve_report)]),
         "fe_last_error": (C.c_char_p, []),
         "fe_launch_count": (C.c_int64, []),
     }
@@ -338,3 +340,15 @@ def fe_solve_rhs(ctx, system, b, nrhs: int, opts: fe_solve_opts | None = None, x
                              _ptr(x_out), 1 if x_on_device else 0, 1 if use_x0 else 0, rep)
     _check(st, "fe_solve_rhs", ok=(FE_OK,) if raise_on_fail else _SOLVE_OK)
     return st, x_out, _reports(rep)
+
+
+def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_opts | None = None,
+                         use_x0: bool = False, raise_on_fail: bool = True):
+    """Solve with the library's fixed device scratch (no allocation during the
+    call); b_dev and x_dev are device buffers [n_dof, nrhs] complex128."""
+    opts = opts or solve_opts()
+    rep = (fe_solve_report * nrhs)()
+    st = load().fe_solve_rhs_noalloc(ctx, system, int(nrhs), _ptr(b_dev), _ptr(x_dev), 1 if use_x0 else 0,
+                                     C.byref(opts), rep)
+    _check(st, "fe_solve_rhs_noalloc", ok=(FE_OK,) if raise_on_fail else _SOLVE_OK)
+    return st, _reports(rep)
