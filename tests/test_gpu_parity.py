@@ -258,3 +258,22 @@ def test_mesh_errors(fe, ctx):
     with pytest.raises(fe.FeError) as e:
         fe.fe_mesh_create_from(ctx, p)
     assert e.value.status == fe.FE_ERR_MESH
+
+
+@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+def test_solve_config2_full_size(fe, ctx, config2, precision):
+    """The 3-wavelength cube at full size (88 998 unknowns) in the launch
+    configuration the benchmark times: FP64 true residual <= 1e-8 with the
+    oracle's matrix, and relative field error <= 1e-6 against the oracle's
+    direct (SuperLU) solution stored by tests/golden/make_reference.py."""
+    from pathlib import Path
+    prob, waves, maps, A = config2
+    ref = np.load(Path(__file__).with_name("golden") / "config2_x.npz")
+    xref = ref["x"].astype(np.complex128)
+    B = fem.rhs(prob, waves, maps=maps)
+    x, rep = _solve(fe, ctx, prob, waves, getattr(fe, f"FE_PREC_{precision}"))
+    res = fem.true_relative_residual(A, x, B)
+    assert rep[0]["status"] == 0, rep
+    assert res.max() <= 1e-8, (res, rep)
+    err = np.linalg.norm(x - xref) / np.linalg.norm(xref)
+    assert err <= 1e-6, err
