@@ -252,9 +252,98 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
     }
 }
 
+// Regular-row classes.  A row is regular when its node is interior and all
+// 8 elements around it are active, of one material, and have no outer face
+// and no PEC neighbour (so no face term reaches the row in any variant).
+__global__ void k_row_class(const uint8_t* __restrict__ mat, int nx, int ny, int nz, const int* __restrict__ node_id,
+                            int n_act, signed char* __restrict__ cls, int* __restrict__ rep) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_act) return;
+    const int id = node_id[r];
+    const int i = id % (nx + 1), j = (id / (nx + 1)) % (ny + 1), k = id / ((nx + 1) * (ny + 1));
+    int c = -1;
+    if (i >= 2 && i <= nx - 2 && j >= 2 && j <= ny - 2 && k >= 2 && k <= nz - 2) {
+        // the 8 elements and their face neighbours lie inside the box
+        const int m = mat[(i - 1) + (int64_t)nx * ((j - 1) + (int64_t)ny * (k - 1))];
+        bool ok = m != kPEC && m < kMaxClasses;
+        for (int ez = 0; ez < 2 && ok; ++ez)
+            for (int ey = 0; ey < 2 && ok; ++ey)
+                for (int ex = 0; ex < 2 && ok; ++ex) {
+                    const int a = i - 1 + ex, b = j - 1 + ey, cc = k - 1 + ez;
+                    if (mat[a + (int64_t)nx * (b + (int64_t)ny * cc)] != m) ok = false;
+                    const int nb[6][3] = {{a - 1, b, cc}, {a + 1, b, cc}, {a, b - 1, cc},
+                                          {a, b + 1, cc}, {a, b, cc - 1}, {a, b, cc + 1}};
+                    for (int f = 0; f < 6 && ok; ++f)
+                        if (mat[nb[f][0] + (int64_t)nx * (nb[f][1] + (int64_t)ny * nb[f][2])] == kPEC) ok = false;
+                }
+        if (ok) c = m;
+    }
+    cls[r] = (signed char)c;
+    if (c >= 0) atomicMin(&rep[c], r);
+}
+
+// One warp per class: copies the 27 blocks of the class's first regular row
+// (bitwise the values every regular row of the class carries) and classifies
+// them.  Entries below 1e-15 of the largest are treated as zero.
+__global__ void k_class_stencil(const double2* __restrict__ val64, int64_t stride, const int* __restrict__ row_ptr,
+                                const int* __restrict__ rep, StencilSet* __restrict__ S) {
+    const int c = blockIdx.x, lane = threadIdx.x;
+    const int r = rep[c];
+    const bool has = r != 0x7fffffff;
+    double2 v[9];
+    double amax = 0.0;
+    if (has && lane < 27) {
+        const int slot = row_ptr[r] + lane;
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            v[q] = val64[q * stride + slot];
+            amax = fmax(amax, fmax(fabs(v[q].x), fabs(v[q].y)));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    const double tiny = 1e-15 * amax;
+    int diag_real = 1;
+    if (has && lane < 27) {
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+                const double2 e = v[3 * al + be];
+                if (fabs(e.y) > tiny || (al != be && fabs(e.x) > tiny)) diag_real = 0;
+            }
+    }
+    diag_real = __all_sync(0xffffffffu, diag_real);
+    if (has && lane < 27) {
+#pragma unroll
+        for (int al = 0; al < 3; ++al) {
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+                const double2 e = v[3 * al + be];
+                S->s64[c][al][lane][be] = e;
+                S->s32[c][al][lane][be] = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
+            }
+            S->dval[c][al][lane] = v[4 * al].x;
+            S->dval32[c][al][lane] = __double2float_rn(v[4 * al].x);
+        }
+    }
+    if (lane == 0) S->kind[c] = has ? (diag_real ? 2 : 1) : 0;
+}
+
+__global__ void k_row_cost(const signed char* __restrict__ cls, const StencilSet* __restrict__ S, int n_act,
+                           int* __restrict__ cost) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n_act) return;
+    const int c = cls[r];
+    const int kind = c >= 0 ? S->kind[c] : 0;
+    cost[r] = kind == 2 ? 1 : (kind == 1 ? 4 : 8);
+}
+
 static void system_free(fe_system* s) {
     cudaStream_t st = s->ctx->stream;
-    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->dinv64, &s->dinv32}) dev_free(st, *b);
+    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->dinv64, &s->dinv32, &s->row_class, &s->stencil,
+                      &s->cost_prefix})
+        dev_free(st, *b);
 }
 
 }  // namespace fe
@@ -343,6 +432,36 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
             set_error("k_assemble launch: %s", cudaGetErrorString(ce));
             return fail(FE_ERR_CUDA);
         }
+    }
+    // regular-row classes and their stencils
+    if ((e = dev_alloc(st, s->row_class, (size_t)m->n_act)) != FE_OK) return fail(e);
+    if ((e = dev_alloc(st, s->stencil, sizeof(StencilSet))) != FE_OK) return fail(e);
+    int* d_rep = (int*)ctx->small.ptr + 16;  // kMaxClasses ints
+    {
+        std::vector<int> big(kMaxClasses, 0x7fffffff);
+        cudaMemcpyAsync(d_rep, big.data(), kMaxClasses * sizeof(int), cudaMemcpyHostToDevice, st);
+        k_row_class<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
+            (const uint8_t*)m->material.ptr, m->nx, m->ny, m->nz, (const int*)m->node_id.ptr, m->n_act,
+            (signed char*)s->row_class.ptr, d_rep);
+        count_launches(1);
+        k_class_stencil<<<kMaxClasses, 32, 0, st>>>((const double2*)s->val64.ptr, s->stride,
+                                                    (const int*)m->row_ptr.ptr, d_rep, (StencilSet*)s->stencil.ptr);
+        count_launches(1);
+        if ((e = dev_alloc(st, s->cost_prefix, (size_t)(m->n_act + 1) * sizeof(int))) != FE_OK) return fail(e);
+        int* cp = (int*)s->cost_prefix.ptr;
+        k_row_cost<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
+            (const signed char*)s->row_class.ptr, (const StencilSet*)s->stencil.ptr, m->n_act, cp);
+        count_launches(1);
+        int* d_total = (int*)ctx->small.ptr + 24;
+        if ((e = scan_exclusive(st, cp, cp, m->n_act, d_total, ctx->scan_tmp)) != FE_OK) return fail(e);
+        cudaMemcpyAsync(cp + m->n_act, d_total, sizeof(int), cudaMemcpyDeviceToDevice, st);
+        cudaMemcpyAsync(ctx->h_small + 24, d_total, sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaError_t ce = cudaStreamSynchronize(st);  // `big` must outlive the copy
+        if (ce != cudaSuccess) {
+            set_error("regular-row classes: %s", cudaGetErrorString(ce));
+            return fail(FE_ERR_CUDA);
+        }
+        s->cost_total = ctx->h_small[24];
     }
     *out = s;
     return FE_OK;

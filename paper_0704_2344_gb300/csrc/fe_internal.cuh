@@ -101,4 +101,31 @@ struct fe_system {
     int64_t stride = 0;              // plane stride: nnzb rounded up to a multiple of 64
     fe::DevBuf val64, val32;         // double2 / float2 [9 * stride]
     fe::DevBuf dinv64, dinv32;       // double2 / float2 [n_act * 9]
+    // Regular rows: interior nodes whose 8 elements are active, of one
+    // material and have no outer or PEC face.  All regular rows of a material
+    // carry the same 27 blocks (same element tables, same summation order), so
+    // the products read them from a per-class stencil instead of the planes.
+    fe::DevBuf row_class;            // int8 [n_act]: class (material < kMaxClasses) or -1
+    fe::DevBuf stencil;              // StencilSet (device)
+    // prefix sum of a per-row cost of the sparse product (explicit row 8,
+    // regular row with a general stencil 4, real diagonal stencil 1): the
+    // product phases split rows across CTAs by equal cost
+    fe::DevBuf cost_prefix;          // int [n_act + 1]
+    int64_t cost_total = 0;
 };
+
+namespace fe {
+constexpr int kMaxClasses = 4;
+// Per-class stencils of regular rows, indexed [class][alpha][block k][beta];
+// kind: 0 = no regular row, 1 = general complex blocks, 2 = real diagonal
+// blocks (the homogeneous interior with eps_r = 1 and s = 1); dval holds the
+// diagonal of kind 2.
+struct StencilSet {
+    int kind[kMaxClasses];
+    int pad[kMaxClasses];
+    double2 s64[kMaxClasses][3][27][3];
+    float2 s32[kMaxClasses][3][27][3];
+    double dval[kMaxClasses][3][27];
+    float dval32[kMaxClasses][3][27];
+};
+}  // namespace fe

@@ -2,6 +2,8 @@
 // products, CTA column sums and the bounded grid barrier.
 #pragma once
 
+#include <type_traits>
+
 #include "fe_internal.cuh"
 
 namespace fe {
@@ -16,6 +18,11 @@ template <>
 struct CplxT<double> {
     using type = double2;
 };
+
+// Regular-row class stencils are used by the complex64 products only (the
+// argument is the real or the complex inner type).
+template <typename T>
+constexpr bool kClassPath = std::is_same<T, float>::value || std::is_same<T, float2>::value;
 
 __device__ __forceinline__ float2 mk(float r, float i) { return make_float2(r, i); }
 __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
@@ -222,6 +229,42 @@ __device__ __forceinline__ int stage_cols(const int* __restrict__ rp, const int*
     for (int j = lane; j < se - sb; j += 32) cols[j] = __ldg(col + sb + j);
     __syncwarp();
     return sb;
+}
+
+// Component alpha of a regular row (all 27 blocks present) from the class
+// stencil: a real diagonal stencil (kind 2) needs one vector entry and one
+// real multiply-add per block; general blocks (kind 1) a full 3x3 product.
+template <typename C, bool kShared>
+__device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ S, int cls, int kind, const int* cols,
+                                                 int al, const C* xs, int xoff) {
+    using Tr = decltype(C{}.x);
+    constexpr bool kF32 = sizeof(C) == 8;
+    Tr ar = 0, ai = 0;
+    if (kind == 2) {
+        const Tr* d = kF32 ? (const Tr*)S->dval32[cls][al] : (const Tr*)S->dval[cls][al];
+#pragma unroll 9
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xi = 3 * cols[kk] + al - xoff;
+            const C xv = kShared ? xs[xi] : ld_cg(xs + xi);
+            const Tr dk = __ldg(d + kk);
+            ar += dk * xv.x;
+            ai += dk * xv.y;
+        }
+    } else {
+        const C* s = kF32 ? (const C*)S->s32[cls][al][0] : (const C*)S->s64[cls][al][0];
+#pragma unroll 3
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xi = 3 * cols[kk] - xoff;
+#pragma unroll
+            for (int be = 0; be < 3; ++be) {
+                const C m = ld_ro(s + 3 * kk + be);
+                const C xv = kShared ? xs[xi + be] : ld_cg(xs + xi + be);
+                ar += m.x * xv.x - m.y * xv.y;
+                ai += m.x * xv.y + m.y * xv.x;
+            }
+        }
+    }
+    return mk(ar, ai);
 }
 
 }  // namespace fe

@@ -54,6 +54,10 @@ struct SolveParams {
     const void* valM;       // matrix in the inner precision
     int64_t stride;         // plane stride of the block values
     const double2* dinv64;  // block-Jacobi inverse, applied in FP64
+    const signed char* row_class;  // regular-row class per row (-1: explicit blocks)
+    const StencilSet* stencil;     // class stencils
+    const int* cost_prefix;        // per-row product cost prefix [n_rows + 1] (product phases split by cost)
+    int64_t cost_total;            // cost_prefix[n_rows] (host copy, sizes the halo buffer)
     const double2* b;
     double2* x;
     double2* r;
@@ -282,12 +286,19 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             if (lane < 30 && row < re) {
                 const int s0 = __ldg(P.rp + row), s1 = __ldg(P.rp + row + 1);
                 const int* rc = cols + (s0 - sb);
-                const C y = row_component<C, kStaged>(valM, P.stride, rc, s0, s1, al, kStaged ? xs : uM,
-                                                      kStaged ? -xshift : 0);
+                // class stencils only in the complex64 kernels (keeps the FP64 kernel's registers)
+                const int cls = (kClassPath<C> && P.row_class) ? __ldg(P.row_class + row) : -1;
+                const int kind = cls >= 0 ? __ldg(&P.stencil->kind[cls]) : 0;
+                const C y = kind ? row_component_class<C, kStaged>(P.stencil, cls, kind, rc, al, kStaged ? xs : uM,
+                                                                   kStaged ? -xshift : 0)
+                                 : row_component<C, kStaged>(valM, P.stride, rc, s0, s1, al, kStaged ? xs : uM,
+                                                             kStaged ? -xshift : 0);
                 const size_t o = (size_t)3 * row + al;
                 w[o] = y;
                 C sy = y;
-                if (refresh) sy = row_component<C, false>(valM, P.stride, rc, s0, s1, al, pM, 0);
+                if (refresh)
+                    sy = kind ? row_component_class<C, false>(P.stencil, cls, kind, rc, al, pM, 0)
+                              : row_component<C, false>(valM, P.stride, rc, s0, s1, al, pM, 0);
                 dots(o, y, refresh, sy);
             }
             __syncwarp();
@@ -354,8 +365,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
     __shared__ double2 s_exch[kThreads];
 
     const int tid = threadIdx.x;
+    // vector phases: equal row counts; product phases: equal product cost
     const int r0 = (int)((int64_t)blockIdx.x * P.n_rows / P.n_cta);
     const int r1 = (int)((int64_t)(blockIdx.x + 1) * P.n_rows / P.n_cta);
+    __shared__ int s_pr[2];
+    if (tid < 2 && !P.cost_prefix) s_pr[tid] = (int)((int64_t)(blockIdx.x + tid) * P.n_rows / P.n_cta);
+    if (tid < 2 && P.cost_prefix) {
+        const int64_t total = P.cost_prefix[P.n_rows];
+        const int64_t target = (int64_t)(blockIdx.x + tid) * total / P.n_cta;
+        int lo = 0, hi = P.n_rows;  // first row whose prefix >= target
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if ((int64_t)P.cost_prefix[mid] < target) lo = mid + 1;
+            else hi = mid;
+        }
+        s_pr[tid] = (blockIdx.x + tid == P.n_cta) ? P.n_rows : lo;
+    }
+    __syncthreads();
+    const int pr0 = s_pr[0], pr1 = s_pr[1];
     const int n_items = (r1 - r0) * R;  // (node, column) pairs owned by this CTA
     const int my_c = tid % R;           // column of every item this thread handles
     const size_t base_o = (size_t)3 * r0 * R;
@@ -394,16 +421,21 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
                     if (s_repl[0]) {
                         int* cols = s_cols + warp * kColsPerWarp;
                         const int al = lane % 3;
-                        for (int rb = r0 + warp * kRowsPerWarpR1; rb < r1; rb += kWarps * kRowsPerWarpR1) {
-                            const int re = min(rb + kRowsPerWarpR1, r1);
+                        for (int rb = pr0 + warp * kRowsPerWarpR1; rb < pr1; rb += kWarps * kRowsPerWarpR1) {
+                            const int re = min(rb + kRowsPerWarpR1, pr1);
                             const int sb = stage_cols(P.rp, P.col, rb, re, cols, lane);
                             const int row = rb + lane / 3;
                             if (lane < 30 && row < re) {
                                 const int s0 = __ldg(P.rp + row), s1 = __ldg(P.rp + row + 1);
                                 const size_t o = (size_t)3 * row + al;
                                 const double2 bv = __ldg(P.b + o);
-                                const double2 y = row_component<double2, false>(P.val64, P.stride, cols + (s0 - sb),
-                                                                                s0, s1, al, P.x, 0);
+                                const int cls = (kClassPath<TM> && P.row_class) ? __ldg(P.row_class + row) : -1;
+                                const int kind = cls >= 0 ? __ldg(&P.stencil->kind[cls]) : 0;
+                                const double2 y =
+                                    kind ? row_component_class<double2, false>(P.stencil, cls, kind, cols + (s0 - sb),
+                                                                               al, P.x, 0)
+                                         : row_component<double2, false>(P.val64, P.stride, cols + (s0 - sb), s0, s1,
+                                                                         al, P.x, 0);
                                 const double2 rv = make_double2(bv.x - y.x, bv.y - y.y);
                                 P.r[o] = rv;
                                 acc[0] += rv.x * rv.x + rv.y * rv.y;
@@ -416,7 +448,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
                     constexpr int kRowsPerWarp = 32 / R;
                     const int c = lane % R;
                     if (s_repl[c]) {
-                        for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1;
+                        for (int row = pr0 + warp * kRowsPerWarp + lane / R; row < pr1;
                              row += kWarps * kRowsPerWarp) {
                             double2 y[3];
                             row_product_colx<double2, false>(P.val64, P.stride, P.col, __ldg(P.rp + row),
@@ -518,15 +550,15 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
             double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             if (P.stage) {
                 int shift = 0;
-                if (!stage_halo<C, R>(P, uM, r0, r1, halo_buf, &s_mbar, mbar_phase, shift)) goto out;
+                if (!stage_halo<C, R>(P, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, shift)) goto out;
                 FE_TRACE_MARK(1);
-                if (!product_phase<TM, R, true>(P, (const C*)halo_buf, shift, r0, r1, s_refresh, s_any_refresh, s_cols,
+                if (!product_phase<TM, R, true>(P, (const C*)halo_buf, shift, pr0, pr1, s_refresh, s_any_refresh, s_cols,
                                                 acc)) {
                     if (tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
                     goto out;
                 }
             } else {
-                if (!product_phase<TM, R, false>(P, nullptr, 0, r0, r1, s_refresh, s_any_refresh, s_cols, acc)) {
+                if (!product_phase<TM, R, false>(P, nullptr, 0, pr0, pr1, s_refresh, s_any_refresh, s_cols, acc)) {
                     if (tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
                     goto out;
                 }
@@ -766,7 +798,8 @@ static fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
     P.n_cta = std::min(ctx->num_sms, std::max(1, P.n_rows));
     P.red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
     P.col_bytes = R == 1 ? (int)(kWarps * kColsPerWarp * sizeof(int)) : 0;
-    const int64_t rows_per_cta = (P.n_rows + P.n_cta - 1) / P.n_cta + 1;
+    // product phases: a CTA gets at most total cost / n_cta (+1 row) of cost >= 1 per row
+    const int64_t rows_per_cta = std::min<int64_t>(P.n_rows, P.cost_total / P.n_cta + 9);
     const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
     P.stage = (P.halo > 0 && (size_t)P.red_bytes + P.col_bytes + (size_t)halo_bytes <= kSmemBudget) ? 1 : 0;
     const size_t dyn = (size_t)P.red_bytes + P.col_bytes + (P.stage ? (size_t)halo_bytes : 0);
@@ -874,6 +907,12 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
         P.valM = fp64 ? s->val64.ptr : s->val32.ptr;
         P.stride = s->stride;
         P.dinv64 = (const double2*)s->dinv64.ptr;
+        // class stencils and cost-balanced product ranges pay off for the
+        // complex64 products; the FP64 products stay explicit and uniform
+        P.row_class = fp64 ? nullptr : (const signed char*)s->row_class.ptr;
+        P.stencil = (const StencilSet*)s->stencil.ptr;
+        P.cost_prefix = fp64 ? nullptr : (const int*)s->cost_prefix.ptr;
+        P.cost_total = fp64 ? (int64_t)m->n_act : s->cost_total;
         P.b = (const double2*)w.b.ptr;
         P.x = (double2*)w.x.ptr;
         P.r = (double2*)w.r.ptr;
@@ -1196,6 +1235,10 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     P.valM = fp64 ? s->val64.ptr : s->val32.ptr;
     P.stride = s->stride;
     P.dinv64 = (const double2*)s->dinv64.ptr;
+    P.row_class = fp64 ? nullptr : (const signed char*)s->row_class.ptr;
+    P.stencil = (const StencilSet*)s->stencil.ptr;
+    P.cost_prefix = fp64 ? nullptr : (const int*)s->cost_prefix.ptr;
+    P.cost_total = fp64 ? (int64_t)m->n_act : s->cost_total;
     P.b = (const double2*)b_dev;
     P.x = (double2*)x_dev;
     P.r = r;
