@@ -77,7 +77,10 @@ typedef enum fe_variant {
 
 typedef enum fe_precision {
     FE_PREC_FP64 = 0,  /* plain method: complex128 matrix, complex128 Krylov loop */
-    FE_PREC_MIXED = 1  /* complex64 Krylov loop inside FP64 iterative refinement */
+    FE_PREC_MIXED = 1, /* complex64 Krylov loop inside FP64 iterative refinement */
+    FE_PREC_DF = 2     /* Krylov products on FP32 pairs ("double-float", about 48 significant bits:
+                          hi = RN32(v), lo = RN32(v - hi), products by error-free transformations on
+                          the FP32 pipes), everything else FP64; converges like FE_PREC_FP64 */
 } fe_precision;
 
 typedef struct fe_options {
@@ -150,7 +153,8 @@ void fe_mesh_destroy(fe_mesh* m);
  * variant's symmetrisation, Section 3.1.4, is applied element by element).
  * Also builds the 3x3 block-Jacobi inverse (the block form of the diagonal
  * preconditioning of Section 3.1.5.1) and, for FE_PREC_MIXED, the
- * round-to-nearest complex64 copies of the matrix and of the inverse.
+ * round-to-nearest complex64 copies of the matrix and of the inverse; for
+ * FE_PREC_DF, the FP32-pair copy of the matrix.
  * ---------------------------------------------------------------------- */
 /* Errors: FE_ERR_INVALID_ARG (freq_hz <= 0, bad precision), FE_ERR_OOM, FE_ERR_CUDA. */
 fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t precision, fe_system** out);
@@ -158,6 +162,25 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
  * vals_c128[nnzb*9*2 doubles], vals_c64[nnzb*9*2 floats] (FE_PREC_MIXED only,
  * else FE_ERR_INVALID_ARG), dinv_c128[n_nodes*9*2 doubles]. */
 fe_status fe_system_export(fe_ctx* ctx, const fe_system* s, void* vals_c128, void* vals_c64, void* dinv_c128);
+/* Regular rows (interior nodes whose eight elements are active, of one
+ * material, with no outer or PEC face) all carry the same 27 blocks per
+ * material; the Krylov products read them from a per-material stencil instead
+ * of the stored blocks.  The counts say how many rows take each path. */
+typedef struct fe_system_stats {
+    int32_t precision;         /* as assembled */
+    int32_t reserved;
+    int64_t n_rows, nnzb;      /* block rows, stored blocks */
+    int64_t rows_general;      /* regular rows with a general 3x3-block stencil */
+    int64_t rows_diagonal;     /* regular rows whose stencil blocks are real multiples of I3 */
+    int64_t blocks_explicit;   /* stored blocks of the other (explicit) rows */
+    int64_t device_bytes;      /* device memory held by the system */
+} fe_system_stats;
+fe_status fe_system_info(const fe_system* s, fe_system_stats* out);
+/* Copies the FP32-pair values of a system assembled with FE_PREC_DF to a
+ * caller-allocated HOST buffer vals_df[nnzb*9*4 floats]: per entry
+ * (re_hi, im_hi, re_lo, im_lo), block-major as vals_c128.  Errors:
+ * FE_ERR_INVALID_ARG (NULL, or the system has no FP32-pair copy). */
+fe_status fe_system_export_df(fe_ctx* ctx, const fe_system* s, void* vals_df);
 void fe_system_destroy(fe_system* s);
 
 /* ------------------------------------------------------------------------
@@ -177,7 +200,9 @@ fe_status fe_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const fe_planewa
 
 /* y = A x for the block matrix of `s` in `precision` (FE_PREC_FP64: complex128
  * vectors and matrix; FE_PREC_MIXED: complex64 vectors and the complex64
- * matrix copy).  x, y: DEVICE buffers [n_dof][nrhs], nrhs >= 1; no aliasing.
+ * matrix copy; FE_PREC_DF: vectors of complex FP32 pairs, 16 bytes per entry
+ * (re_hi, im_hi, re_lo, im_lo), and the FP32-pair matrix copy).  x, y:
+ * DEVICE buffers [n_dof][nrhs], nrhs >= 1; no aliasing.
  * This is the sparse product at the heart of the Krylov loop (Section 3.1.5.1). */
 fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y);
 
@@ -190,7 +215,10 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
  * and the preconditioner stay FP64; each time the recursive residual has
  * dropped by `reliable`, the FP64 true residual b - A x replaces it and the
  * directions restart (FP64 iterative refinement around complex64 Krylov
- * passes).  The true residual decides convergence: ||b - A x|| / ||b|| <= tol
+ * passes).  FE_PREC_DF runs those products on the FP32-pair copy (about
+ * 48 significant bits on the FP32 pipes, which GB300 issues at 64 times the
+ * FP64 rate) and, like FE_PREC_FP64, keeps the directions across true-residual
+ * refreshes.  The true residual decides convergence: ||b - A x|| / ||b|| <= tol
  * for every right-hand side.  Up to
  * rhs_tile right-hand sides are solved together in one persistent device
  * launch.
@@ -257,6 +285,95 @@ fe_status fe_solve_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void
  * Errors: as fe_solve_rhs. */
 fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b_dev, void* x_dev,
                                int32_t use_x0, const fe_solve_opts* o, fe_solve_report* rep);
+
+/* ------------------------------------------------------------------------
+ * Serving: a queue of independent scattering problems (each its own voxel
+ * box, frequency and plane waves) solved with continuous batching.  The
+ * server owns a worker thread and a CUDA stream of its own on the device of
+ * the context passed to fe_serve_create (whose options, variant, abc_sigma
+ * and penalty_s, apply to every request; that context stays free for the
+ * caller).  The worker admits queued requests in arrival order while the
+ * sum of their estimated device memory stays within the budget, builds each
+ * admitted request's mesh, system (Eqs. 1-4) and right-hand sides, and packs
+ * the ready requests of one right-hand-side tile width (1, 2, 4, 8, 16 or
+ * 32 after padding with zero columns) into one persistent cooperative
+ * solve launch: every request gets its own range of CTAs, synchronises only
+ * among them and is solved exactly as fe_solve_batch would solve it.
+ * Requests that arrive during a launch join the next one.
+ * ---------------------------------------------------------------------- */
+typedef struct fe_serve_opts {
+    int32_t precision;     /* FE_PREC_FP64 (default), FE_PREC_MIXED or FE_PREC_DF, for every request */
+    double tol;            /* true relative residual target; default 1e-8 */
+    double reliable;       /* FE_PREC_MIXED refinement trigger; default 1e-4 */
+    int32_t max_iter;      /* default 20000 */
+    int32_t max_outer;     /* default 200 */
+    int64_t hbm_budget;    /* device bytes for admitted requests; 0: 80 % of the free memory at creation */
+    int32_t max_ctas;      /* CTAs of one launch, 1..one per SM; 0: one per SM */
+    int32_t work_per_cta;  /* packing target, block rows x tile width per CTA; 0: 2048 */
+} fe_serve_opts;
+void fe_serve_opts_default(fe_serve_opts* o);
+
+typedef struct fe_request {
+    fe_mesh_desc mesh;          /* host pointers only (material_on_device = 0); copied by fe_serve_submit */
+    double freq_hz;             /* > 0 */
+    int32_t nrhs;               /* 1..32 */
+    const fe_planewave* waves;  /* host, nrhs entries; copied */
+} fe_request;
+
+typedef struct fe_result {
+    int32_t status;             /* FE_OK, or why the request failed (FE_ERR_MESH, FE_ERR_OOM, FE_ERR_NOT_CONVERGED ...) */
+    int32_t nrhs;
+    int64_t n_dof;              /* 3 x active nodes (0 when the mesh failed) */
+    const fe_complex* x;        /* [n_dof][nrhs] total H at the active nodes, ranked as everywhere else;
+                                   NULL when no solve ran.  Owned by the server until fe_serve_release. */
+    const int32_t* node_id;     /* [n_dof / 3] grid node id of every rank; owned like x */
+    const fe_solve_report* reports; /* [nrhs] per right-hand side; owned like x (NULL when no solve ran) */
+    double t_submit, t_admit, t_done; /* seconds since fe_serve_create */
+    int32_t batch_jobs;         /* requests in the launch that solved it */
+    int32_t batch_ctas;         /* CTAs it had in that launch */
+    const char* message;        /* "" or the error text; owned like x */
+} fe_result;
+
+typedef struct fe_serve_stats {
+    int64_t submitted, completed, failed;
+    int64_t launches;           /* persistent solve launches */
+    int64_t jobs_launched;      /* requests summed over launches */
+    int64_t budget_bytes;       /* admission budget */
+    int64_t peak_admitted_bytes;/* largest sum of admitted estimates */
+    double solve_device_s;      /* device time of the solve launches (CUDA events) */
+} fe_serve_stats;
+
+/* Errors: FE_ERR_INVALID_ARG (NULL, options out of range), FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_serve_create(fe_ctx* ctx, const fe_serve_opts* o, fe_server** out);
+/* Non-blocking.  Validates and copies the request, returns its ticket (> 0).
+ * Errors: FE_ERR_INVALID_ARG (NULL pointers, sizes, nrhs, a device material
+ * pointer, a stopped server).  Mesh rules are checked later: such a request
+ * finishes with status FE_ERR_MESH. */
+fe_status fe_serve_submit(fe_server* srv, const fe_request* r, uint64_t* ticket);
+/* FE_PENDING while the request is queued or running; FE_OK with *out filled
+ * once it has finished, whether it succeeded or not (out->status says which);
+ * FE_ERR_INVALID_ARG for an unknown or released ticket. */
+fe_status fe_serve_poll(fe_server* srv, uint64_t ticket, fe_result* out);
+/* As fe_serve_poll, but blocks until the request finishes or timeout_s
+ * seconds pass (then FE_PENDING). */
+fe_status fe_serve_wait(fe_server* srv, uint64_t ticket, double timeout_s, fe_result* out);
+/* Frees a finished request's result; the pointers in its fe_result die.
+ * Errors: FE_ERR_INVALID_ARG (unknown ticket), FE_PENDING (not finished). */
+fe_status fe_serve_release(fe_server* srv, uint64_t ticket);
+fe_status fe_serve_info(fe_server* srv, fe_serve_stats* out);
+/* Stops the worker after its current launch, drops unfinished requests and
+ * frees everything, including unreleased results. */
+void fe_serve_destroy(fe_server* srv);
+/* The server's packing rule, a host-only function (no device work): given n
+ * ready requests in arrival order with their block rows and tile widths,
+ * fills n_cta[i] (0: not in this launch) for one launch of at most max_ctas
+ * CTAs and returns how many requests it takes.  The oldest request is always
+ * taken; others of its width follow in order while their CTA demand,
+ * ceil(rows x width / work_per_cta) clamped to 1..rows, fits; CTAs left over
+ * go one at a time to the taken request with the most work per CTA while it
+ * keeps at least work_per_cta / 4 per CTA. */
+int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t work_per_cta,
+                      int32_t* n_cta);
 
 /* Device-side statistics of the most recent fe_solve_batch / fe_solve_rhs
  * call on this context, measured with CUDA events on the context stream

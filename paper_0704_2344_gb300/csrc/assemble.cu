@@ -15,11 +15,18 @@
 // the diagonal block for the block-Jacobi preconditioner.
 #include "fe_internal.cuh"
 
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <vector>
 
 namespace fe {
+
+// FP32 pair of a complex128 value: hi = RN32(v), lo = RN32(v - hi) per part.
+__device__ __forceinline__ float4 df_pair(double2 v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+}
 
 struct Cx {
     double re, im;
@@ -138,9 +145,9 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                                                   int n_mat, const int* __restrict__ node_id,
                                                   const int* __restrict__ row_ptr,
                                                   const double2* __restrict__ tab, double2* __restrict__ val64,
-                                                  float2* __restrict__ val32, double2* __restrict__ dinv64,
-                                                  float2* __restrict__ dinv32, int n_act, int64_t stride,
-                                                  int* __restrict__ status) {
+                                                  float2* __restrict__ val32, float4* __restrict__ valdf,
+                                                  double2* __restrict__ dinv64, float2* __restrict__ dinv32,
+                                                  int n_act, int64_t stride, int* __restrict__ status) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_act) return;
@@ -218,6 +225,10 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
 #pragma unroll
         for (int q = 0; q < 9; ++q)
             val32[q * stride + slot] = make_float2(__double2float_rn(acc[q].x), __double2float_rn(acc[q].y));
+    }
+    if (valdf) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) valdf[q * stride + slot] = df_pair(acc[q]);
     }
     if (lane == 13) {  // diagonal block: 3x3 complex inverse by cofactors
         Cx A[3][3];
@@ -322,27 +333,56 @@ __global__ void k_class_stencil(const double2* __restrict__ val64, int64_t strid
                 const double2 e = v[3 * al + be];
                 S->s64[c][al][lane][be] = e;
                 S->s32[c][al][lane][be] = make_float2(__double2float_rn(e.x), __double2float_rn(e.y));
+                S->sdf[c][al][lane][be] = df_pair(e);
             }
             S->dval[c][al][lane] = v[4 * al].x;
             S->dval32[c][al][lane] = __double2float_rn(v[4 * al].x);
+            const float dh = __double2float_rn(v[4 * al].x);
+            S->dvaldf[c][al][lane] = make_float2(dh, __double2float_rn(v[4 * al].x - (double)dh));
         }
     }
     if (lane == 0) S->kind[c] = has ? (diag_real ? 2 : 1) : 0;
 }
 
+// Rows on each product path: counts[0] general-stencil rows, counts[1] real
+// diagonal stencil rows, counts[2] blocks of the explicit rows.
+__global__ void k_class_counts(const signed char* __restrict__ cls, const StencilSet* __restrict__ S,
+                               const int* __restrict__ row_ptr, int n_act, unsigned long long* __restrict__ counts) {
+    unsigned long long c1 = 0, c2 = 0, cb = 0;
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n_act; r += gridDim.x * blockDim.x) {
+        const int c = cls[r];
+        const int kind = c >= 0 ? S->kind[c] : 0;
+        c1 += kind == 1;
+        c2 += kind == 2;
+        cb += kind == 0 ? (unsigned long long)(row_ptr[r + 1] - row_ptr[r]) : 0ull;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c1 += __shfl_xor_sync(0xffffffffu, c1, o);
+        c2 += __shfl_xor_sync(0xffffffffu, c2, o);
+        cb += __shfl_xor_sync(0xffffffffu, cb, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(counts, c1);
+        atomicAdd(counts + 1, c2);
+        atomicAdd(counts + 2, cb);
+    }
+}
+
+// Per-row product cost with weights w_explicit, w_general, w_diagonal.
 __global__ void k_row_cost(const signed char* __restrict__ cls, const StencilSet* __restrict__ S, int n_act,
-                           int* __restrict__ cost) {
+                           int w0, int w1, int w2, int* __restrict__ cost) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_act) return;
     const int c = cls[r];
     const int kind = c >= 0 ? S->kind[c] : 0;
-    cost[r] = kind == 2 ? 1 : (kind == 1 ? 4 : 8);
+    cost[r] = kind == 2 ? w2 : (kind == 1 ? w1 : w0);
 }
 
 static void system_free(fe_system* s) {
     cudaStream_t st = s->ctx->stream;
-    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->dinv64, &s->dinv32, &s->row_class, &s->stencil,
-                      &s->cost_prefix})
+    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->row_class,
+                      &s->stencil, &s->cost_prefix, &s->cost_prefix_alu})
         dev_free(st, *b);
 }
 
@@ -358,8 +398,8 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         return FE_ERR_INVALID_ARG;
     }
     *out = nullptr;
-    if (!(freq_hz > 0.0) || (precision != FE_PREC_FP64 && precision != FE_PREC_MIXED)) {
-        set_error("fe_assemble: frequency must be > 0 and precision FP64 or MIXED");
+    if (!(freq_hz > 0.0) || (precision != FE_PREC_FP64 && precision != FE_PREC_MIXED && precision != FE_PREC_DF)) {
+        set_error("fe_assemble: frequency must be > 0 and precision FP64, MIXED or DF");
         return FE_ERR_INVALID_ARG;
     }
     if (m->n_mat > 64) {
@@ -396,6 +436,9 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         if ((e = dev_alloc(st, s->val32, (size_t)s->stride * 9 * sizeof(float2))) != FE_OK) return fail(e);
         if ((e = dev_alloc(st, s->dinv32, (size_t)m->n_act * 9 * sizeof(float2))) != FE_OK) return fail(e);
     }
+    if (precision == FE_PREC_DF) {
+        if ((e = dev_alloc(st, s->valdf, (size_t)s->stride * 9 * sizeof(float4))) != FE_OK) return fail(e);
+    }
     TableParams P{};
     for (int a = 0; a < 3; ++a) P.h[a] = m->h[a];
     P.k0 = s->k0;
@@ -423,8 +466,8 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
     k_assemble<<<blocks, threads, 0, st>>>((const uint8_t*)m->material.ptr, m->nx, m->ny, m->nz, m->n_mat,
                                            (const int*)m->node_id.ptr, (const int*)m->row_ptr.ptr,
                                            (const double2*)s->tables.ptr, (double2*)s->val64.ptr,
-                                           (float2*)s->val32.ptr, (double2*)s->dinv64.ptr, (float2*)s->dinv32.ptr,
-                                           m->n_act, s->stride, d_status);
+                                           (float2*)s->val32.ptr, (float4*)s->valdf.ptr, (double2*)s->dinv64.ptr,
+                                           (float2*)s->dinv32.ptr, m->n_act, s->stride, d_status);
     {
         count_launches(1);
         cudaError_t ce = cudaGetLastError();
@@ -447,23 +490,84 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         k_class_stencil<<<kMaxClasses, 32, 0, st>>>((const double2*)s->val64.ptr, s->stride,
                                                     (const int*)m->row_ptr.ptr, d_rep, (StencilSet*)s->stencil.ptr);
         count_launches(1);
-        if ((e = dev_alloc(st, s->cost_prefix, (size_t)(m->n_act + 1) * sizeof(int))) != FE_OK) return fail(e);
-        int* cp = (int*)s->cost_prefix.ptr;
-        k_row_cost<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
-            (const signed char*)s->row_class.ptr, (const StencilSet*)s->stencil.ptr, m->n_act, cp);
-        count_launches(1);
+        // product cost prefixes: memory weights (explicit 8, general stencil 4,
+        // real diagonal stencil 1) for the complex64 products, arithmetic
+        // weights (7, 6, 1) for the double-float products
+        const int weights[2][3] = {{8, 4, 1}, {7, 6, 1}};
+        DevBuf* bufs[2] = {&s->cost_prefix, &s->cost_prefix_alu};
         int* d_total = (int*)ctx->small.ptr + 24;
-        if ((e = scan_exclusive(st, cp, cp, m->n_act, d_total, ctx->scan_tmp)) != FE_OK) return fail(e);
-        cudaMemcpyAsync(cp + m->n_act, d_total, sizeof(int), cudaMemcpyDeviceToDevice, st);
-        cudaMemcpyAsync(ctx->h_small + 24, d_total, sizeof(int), cudaMemcpyDeviceToHost, st);
+        for (int k = 0; k < 2; ++k) {
+            if ((e = dev_alloc(st, *bufs[k], (size_t)(m->n_act + 1) * sizeof(int))) != FE_OK) return fail(e);
+            int* cp = (int*)bufs[k]->ptr;
+            k_row_cost<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
+                (const signed char*)s->row_class.ptr, (const StencilSet*)s->stencil.ptr, m->n_act, weights[k][0],
+                weights[k][1], weights[k][2], cp);
+            count_launches(1);
+            if ((e = scan_exclusive(st, cp, cp, m->n_act, d_total + k, ctx->scan_tmp)) != FE_OK) return fail(e);
+            cudaMemcpyAsync(cp + m->n_act, d_total + k, sizeof(int), cudaMemcpyDeviceToDevice, st);
+        }
+        unsigned long long* d_counts = (unsigned long long*)((int*)ctx->small.ptr + 32);
+        cudaMemsetAsync(d_counts, 0, 3 * sizeof(unsigned long long), st);
+        k_class_counts<<<std::max(1, std::min(1024, (m->n_act + 255) / 256)), 256, 0, st>>>(
+            (const signed char*)s->row_class.ptr, (const StencilSet*)s->stencil.ptr, (const int*)m->row_ptr.ptr,
+            m->n_act, d_counts);
+        count_launches(1);
+        cudaMemcpyAsync(ctx->h_small + 24, d_total, 2 * sizeof(int), cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(ctx->h_small + 32, d_counts, 3 * sizeof(unsigned long long), cudaMemcpyDeviceToHost, st);
         cudaError_t ce = cudaStreamSynchronize(st);  // `big` must outlive the copy
         if (ce != cudaSuccess) {
             set_error("regular-row classes: %s", cudaGetErrorString(ce));
             return fail(FE_ERR_CUDA);
         }
         s->cost_total = ctx->h_small[24];
+        s->cost_total_alu = ctx->h_small[25];
+        const unsigned long long* hc = (const unsigned long long*)(ctx->h_small + 32);
+        s->rows_general = (int64_t)hc[0];
+        s->rows_diagonal = (int64_t)hc[1];
+        s->blocks_explicit = (int64_t)hc[2];
     }
     *out = s;
+    return FE_OK;
+}
+
+fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
+    if (!s || !out) {
+        set_error("fe_system_info: NULL argument");
+        return FE_ERR_INVALID_ARG;
+    }
+    const fe_mesh* m = s->mesh;
+    out->precision = s->precision;
+    out->reserved = 0;
+    out->n_rows = m->n_act;
+    out->nnzb = m->nnzb;
+    out->rows_general = s->rows_general;
+    out->rows_diagonal = s->rows_diagonal;
+    out->blocks_explicit = s->blocks_explicit;
+    int64_t bytes = 0;
+    for (const DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->row_class,
+                            &s->stencil, &s->cost_prefix, &s->cost_prefix_alu})
+        bytes += (int64_t)b->bytes;
+    out->device_bytes = bytes;
+    return FE_OK;
+}
+
+fe_status fe_system_export_df(fe_ctx* ctx, const fe_system* s, void* vals_df) {
+    if (!ctx || !s || !vals_df) {
+        set_error("fe_system_export_df: NULL argument");
+        return FE_ERR_INVALID_ARG;
+    }
+    if (!s->valdf.ptr) {
+        set_error("fe_system_export_df: no FP32-pair copy (system not assembled with FE_PREC_DF)");
+        return FE_ERR_INVALID_ARG;
+    }
+    cudaStream_t st = ctx->stream;
+    const fe_mesh* m = s->mesh;
+    std::vector<float4> tmp((size_t)s->stride * 9);
+    FE_CUDA(cudaMemcpyAsync(tmp.data(), s->valdf.ptr, tmp.size() * sizeof(float4), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    float4* out = (float4*)vals_df;
+    for (int64_t b = 0; b < m->nnzb; ++b)
+        for (int q = 0; q < 9; ++q) out[(size_t)b * 9 + q] = tmp[(size_t)q * s->stride + b];
     return FE_OK;
 }
 

@@ -100,6 +100,7 @@ struct fe_system {
     // warp reading one entry of consecutive blocks reads consecutive memory.
     int64_t stride = 0;              // plane stride: nnzb rounded up to a multiple of 64
     fe::DevBuf val64, val32;         // double2 / float2 [9 * stride]
+    fe::DevBuf valdf;                // float4 [9 * stride]: FP32 pairs (re_hi, im_hi, re_lo, im_lo), FE_PREC_DF
     fe::DevBuf dinv64, dinv32;       // double2 / float2 [n_act * 9]
     // Regular rows: interior nodes whose 8 elements are active, of one
     // material and have no outer or PEC face.  All regular rows of a material
@@ -112,6 +113,11 @@ struct fe_system {
     // product phases split rows across CTAs by equal cost
     fe::DevBuf cost_prefix;          // int [n_act + 1]
     int64_t cost_total = 0;
+    // the same with arithmetic weights (explicit 7, general stencil 6, real
+    // diagonal stencil 1) for the ALU-bound double-float products
+    fe::DevBuf cost_prefix_alu;      // int [n_act + 1]
+    int64_t cost_total_alu = 0;
+    int64_t rows_general = 0, rows_diagonal = 0, blocks_explicit = 0;  // rows per product path
 };
 
 namespace fe {
@@ -127,5 +133,7 @@ struct StencilSet {
     float2 s32[kMaxClasses][3][27][3];
     double dval[kMaxClasses][3][27];
     float dval32[kMaxClasses][3][27];
+    float4 sdf[kMaxClasses][3][27][3];   // FP32 pairs of s64
+    float2 dvaldf[kMaxClasses][3][27];   // FP32 pairs (hi, lo) of dval
 };
 }  // namespace fe

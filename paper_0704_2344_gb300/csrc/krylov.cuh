@@ -21,8 +21,45 @@ struct CplxT<double> {
 
 // Regular-row class stencils are used by the complex64 products only (the
 // argument is the real or the complex inner type).
+// Tag of the double-float inner precision: a complex value as FP32 pairs in
+// one float4 (re_hi, im_hi, re_lo, im_lo) with hi = RN32(v), lo = RN32(v - hi).
+struct DFloat {};
+template <>
+struct CplxT<DFloat> {
+    using type = float4;
+};
+
 template <typename T>
-constexpr bool kClassPath = std::is_same<T, float>::value || std::is_same<T, float2>::value;
+constexpr bool kClassPath = std::is_same<T, float>::value || std::is_same<T, float2>::value ||
+                            std::is_same<T, DFloat>::value || std::is_same<T, float4>::value;
+
+// (sh, sl) += a * x for FP32 pairs a = (ah, al), x = (xh, xl).  The rounding
+// error of ah*xh is exact with one FMA and collects the cross terms ah*xl and
+// al*xh (al*xl, about 2^-48 relative, is dropped); the rounded product joins
+// sh by Knuth's TwoSum, whose error term is exact as well (error-free
+// transformations, Knuth, TAOCP vol. 2, 4.2.2; Ogita, Rump and Oishi, 2005).
+// The _rn intrinsics keep the compiler from contracting or reordering them.
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float xh, float xl) {
+    const float p = __fmul_rn(ah, xh);
+    float e = __fmaf_rn(ah, xh, -p);
+    e = __fmaf_rn(ah, xl, e);
+    e = __fmaf_rn(al, xh, e);
+    const float t = __fadd_rn(sh, p);
+    const float v = __fsub_rn(t, sh);
+    const float err = __fadd_rn(__fsub_rn(sh, __fsub_rn(t, v)), __fsub_rn(p, v));
+    sh = t;
+    sl = __fadd_rn(sl, __fadd_rn(err, e));
+}
+
+// acc = (re_hi, re_lo, im_hi, im_lo) += m * x for complex FP32 pairs.
+__device__ __forceinline__ void dfc_mac(float (&acc)[4], const float4& m, const float4& x) {
+    df_mac(acc[0], acc[1], m.x, m.z, x.x, x.z);
+    df_mac(acc[0], acc[1], -m.y, -m.w, x.y, x.w);
+    df_mac(acc[2], acc[3], m.x, m.z, x.y, x.w);
+    df_mac(acc[2], acc[3], m.y, m.w, x.x, x.z);
+}
+
+__device__ __forceinline__ float4 df_result(const float (&acc)[4]) { return make_float4(acc[0], acc[2], acc[1], acc[3]); }
 
 __device__ __forceinline__ float2 mk(float r, float i) { return make_float2(r, i); }
 __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
@@ -152,6 +189,27 @@ template <typename C, bool kShared>
 __device__ __forceinline__ void row_product_colx(const C* __restrict__ val, int64_t stride, const int* __restrict__ col,
                                                  int s0, int s1, const C* xs, int xoff, int ldx, int c, C& y0, C& y1,
                                                  C& y2) {
+  if constexpr (std::is_same<C, float4>::value) {
+    float a[3][4] = {};
+    int cb = s1 > s0 ? __ldg(col + s0) : 0;
+    for (int s = s0; s < s1; ++s) {
+        const int cb_next = __ldg(col + min(s + 1, s1 - 1));
+        float4 xv[3];
+#pragma unroll
+        for (int be = 0; be < 3; ++be) {
+            const int xi = (3 * cb + be) * ldx + c - xoff;
+            xv[be] = kShared ? xs[xi] : ld_cg(xs + xi);
+        }
+#pragma unroll
+        for (int al = 0; al < 3; ++al)
+#pragma unroll
+            for (int be = 0; be < 3; ++be) dfc_mac(a[al], ld_ro(val + (3 * al + be) * stride + s), xv[be]);
+        cb = cb_next;
+    }
+    y0 = df_result(a[0]);
+    y1 = df_result(a[1]);
+    y2 = df_result(a[2]);
+  } else {
     using Tr = decltype(C{}.x);
     Tr a[6] = {0, 0, 0, 0, 0, 0};
     int cb = s1 > s0 ? __ldg(col + s0) : 0;
@@ -176,6 +234,7 @@ __device__ __forceinline__ void row_product_colx(const C* __restrict__ val, int6
     y0 = mk(a[0], a[1]);
     y1 = mk(a[2], a[3]);
     y2 = mk(a[4], a[5]);
+  }
 }
 
 }  // namespace fe
@@ -191,6 +250,22 @@ template <typename C, bool kShared>
 __device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t stride, const int* cols, int s0, int s1,
                                            int al, const C* xs, int xoff) {
     // cols: the row's column indices in shared memory, cols[s - s0]
+  if constexpr (std::is_same<C, float4>::value) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    const float4* v0 = val + (3 * al) * stride;
+    const float4* v1 = v0 + stride;
+    const float4* v2 = v1 + stride;
+    for (int s = s0; s < s1; ++s) {
+        const int xa = 3 * cols[s - s0] - xoff;
+        const float4 m0 = ld_ro(v0 + s), m1 = ld_ro(v1 + s), m2 = ld_ro(v2 + s);
+        const float4 x0 = kShared ? xs[xa] : ld_cg(xs + xa), x1 = kShared ? xs[xa + 1] : ld_cg(xs + xa + 1),
+                     x2 = kShared ? xs[xa + 2] : ld_cg(xs + xa + 2);
+        dfc_mac(acc, m0, x0);
+        dfc_mac(acc, m1, x1);
+        dfc_mac(acc, m2, x2);
+    }
+    return df_result(acc);
+  } else {
     using Tr = decltype(C{}.x);
     Tr ar = 0, ai = 0, br = 0, bi = 0;
     const C* v0 = val + (3 * al) * stride;
@@ -219,6 +294,7 @@ __device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t st
         ai += m0.x * x0.y + m0.y * x0.x + m1.x * x1.y + m1.y * x1.x + m2.x * x2.y + m2.y * x2.x;
     }
     return mk(ar + br, ai + bi);
+  }
 }
 
 // Copies the column indices of the warp's rows [rb, re) into shared memory
@@ -237,6 +313,29 @@ __device__ __forceinline__ int stage_cols(const int* __restrict__ rp, const int*
 template <typename C, bool kShared>
 __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ S, int cls, int kind, const int* cols,
                                                  int al, const C* xs, int xoff) {
+  if constexpr (std::is_same<C, float4>::value) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    if (kind == 2) {
+        const float2* d = S->dvaldf[cls][al];
+#pragma unroll 9
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xi = 3 * cols[kk] + al - xoff;
+            const float4 xv = kShared ? xs[xi] : ld_cg(xs + xi);
+            const float2 dk = __ldg(d + kk);
+            df_mac(acc[0], acc[1], dk.x, dk.y, xv.x, xv.z);
+            df_mac(acc[2], acc[3], dk.x, dk.y, xv.y, xv.w);
+        }
+    } else {
+        const float4* sp = S->sdf[cls][al][0];
+#pragma unroll 3
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xi = 3 * cols[kk] - xoff;
+#pragma unroll
+            for (int be = 0; be < 3; ++be) dfc_mac(acc, ld_ro(sp + 3 * kk + be), kShared ? xs[xi + be] : ld_cg(xs + xi + be));
+        }
+    }
+    return df_result(acc);
+  } else {
     using Tr = decltype(C{}.x);
     constexpr bool kF32 = sizeof(C) == 8;
     Tr ar = 0, ai = 0;
@@ -265,6 +364,7 @@ __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ 
         }
     }
     return mk(ar, ai);
+  }
 }
 
 }  // namespace fe

@@ -96,10 +96,10 @@ struct SolveParams {
 // kDevTimeout and every CTA leaves at its next barrier.
 // ---------------------------------------------------------------------------
 template <int NV>
-__device__ __noinline__ bool grid_reduce(const SolveParams& P, const double* s_in, double* s_out) {
+__device__ __noinline__ bool grid_reduce(const SolveParams& P, int cta, const double* s_in, double* s_out) {
     __shared__ int s_last, s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = threadIdx.x; v < NV; v += kThreads) P.partial[(size_t)blockIdx.x * NV + v] = s_in[v];
+    for (int v = threadIdx.x; v < NV; v += kThreads) P.partial[(size_t)cta * NV + v] = s_in[v];
     __syncthreads();
     volatile unsigned* vgen = &P.sync->gen;
     volatile int* verr = &P.sync->err;
@@ -184,6 +184,9 @@ __device__ __forceinline__ C cfma(C a, C b, C c) {  // a * b + c
 __device__ __forceinline__ float2 to_c64(double2 a) { return make_float2((float)a.x, (float)a.y); }
 __device__ __forceinline__ double2 to_c128(float2 a) { return make_double2(a.x, a.y); }
 __device__ __forceinline__ double2 to_c128(double2 a) { return a; }
+__device__ __forceinline__ double2 to_c128(float4 a) {  // FP32 pair -> FP64
+    return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+}
 template <typename C>
 __device__ __forceinline__ C from_c128(double2 a);
 template <>
@@ -193,6 +196,11 @@ __device__ __forceinline__ float2 from_c128<float2>(double2 a) {
 template <>
 __device__ __forceinline__ double2 from_c128<double2>(double2 a) {
     return a;
+}
+template <>
+__device__ __forceinline__ float4 from_c128<float4>(double2 a) {  // FP64 -> FP32 pair
+    const float rh = __double2float_rn(a.x), ih = __double2float_rn(a.y);
+    return make_float4(rh, ih, __double2float_rn(a.x - (double)rh), __double2float_rn(a.y - (double)ih));
 }
 
 // z = Dinv r for one node and column (3x3 complex block times 3-vector) in
@@ -327,7 +335,7 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
 
 #define FE_TRACE_MARK(k)                                                                        \
     do {                                                                                        \
-        if (P.trace && tid == 0 && trace_it < kTraceIters && blockIdx.x == gridDim.x / 2)       \
+        if (P.trace && tid == 0 && trace_it < kTraceIters && cta == P.n_cta / 2)       \
             P.trace[((size_t)trace_it) * kTracePhases + (k)] = globaltimer_ns();                 \
     } while (0)
 
@@ -344,12 +352,12 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
 //       memory).
 // Grid barriers separate the phases; [A] and [R] end in fused reductions.
 template <typename TM, int R>
-__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
+__device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) {
     using C = typename CplxT<TM>::type;
     C* uM = (C*)P.uM;
     C* pM = (C*)P.pM;
     const C* wv = (const C*)P.w;
-    constexpr bool kSplit = sizeof(C) != sizeof(double2);  // inner copies are separate buffers
+    constexpr bool kSplit = !std::is_same<C, double2>::value;  // inner copies are separate buffers
 
     extern __shared__ __align__(128) char dyn[];
     double* s_red = (double*)dyn;
@@ -366,20 +374,20 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
 
     const int tid = threadIdx.x;
     // vector phases: equal row counts; product phases: equal product cost
-    const int r0 = (int)((int64_t)blockIdx.x * P.n_rows / P.n_cta);
-    const int r1 = (int)((int64_t)(blockIdx.x + 1) * P.n_rows / P.n_cta);
+    const int r0 = (int)((int64_t)cta * P.n_rows / P.n_cta);
+    const int r1 = (int)((int64_t)(cta + 1) * P.n_rows / P.n_cta);
     __shared__ int s_pr[2];
-    if (tid < 2 && !P.cost_prefix) s_pr[tid] = (int)((int64_t)(blockIdx.x + tid) * P.n_rows / P.n_cta);
+    if (tid < 2 && !P.cost_prefix) s_pr[tid] = (int)((int64_t)(cta + tid) * P.n_rows / P.n_cta);
     if (tid < 2 && P.cost_prefix) {
         const int64_t total = P.cost_prefix[P.n_rows];
-        const int64_t target = (int64_t)(blockIdx.x + tid) * total / P.n_cta;
+        const int64_t target = (int64_t)(cta + tid) * total / P.n_cta;
         int lo = 0, hi = P.n_rows;  // first row whose prefix >= target
         while (lo < hi) {
             const int mid = (lo + hi) >> 1;
             if ((int64_t)P.cost_prefix[mid] < target) lo = mid + 1;
             else hi = mid;
         }
-        s_pr[tid] = (blockIdx.x + tid == P.n_cta) ? P.n_rows : lo;
+        s_pr[tid] = (cta + tid == P.n_cta) ? P.n_rows : lo;
     }
     __syncthreads();
     const int pr0 = s_pr[0], pr1 = s_pr[1];
@@ -409,7 +417,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
     }
     if (tid == 0) s_any_repl = 1;
     __syncthreads();
-    if (!grid_reduce<0>(P, s_in, s_out)) goto out;
+    if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
 
     for (;;) {
         if (s_any_repl) {
@@ -466,7 +474,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
                     }
                 }
                 cta_colsum<R, 2>(acc, s_red, s_in);
-                if (!grid_reduce<2 * R>(P, s_in, s_out)) goto out;
+                if (!grid_reduce<2 * R>(P, cta, s_in, s_out)) goto out;
             }
             if (tid < R) {
                 const int c = tid;
@@ -536,7 +544,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
                 s_any_refresh = refr;
                 s_any_repl = 0;
             }
-            if (!grid_reduce<0>(P, s_in, s_out)) goto out;
+            if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
             {
                 int any = 0;
                 for (int c = 0; c < R; ++c) any |= !s_done[c];
@@ -566,12 +574,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
             FE_TRACE_MARK(2);
             if (s_any_refresh) {
                 cta_colsum<R, 11>(acc, s_red, s_in);
-                if (!grid_reduce<11 * R>(P, s_in, s_out)) goto out;
+                if (!grid_reduce<11 * R>(P, cta, s_in, s_out)) goto out;
             } else {
                 double a5[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
                 cta_colsum<R, 5>(a5, s_red, s_in);
                 FE_TRACE_MARK(3);
-                if (!grid_reduce<5 * R>(P, s_in, s_out)) goto out;
+                if (!grid_reduce<5 * R>(P, cta, s_in, s_out)) goto out;
             }
             FE_TRACE_MARK(4);
         }
@@ -716,17 +724,51 @@ __global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
             }
         }
         FE_TRACE_MARK(6);
-        if (!grid_reduce<0>(P, s_in, s_out)) goto out;
+        if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
         FE_TRACE_MARK(7);
         ++trace_it;
     }
 out:
-    if (blockIdx.x == 0 && tid < R) {
+    if (cta == 0 && tid < R) {
         P.rep_status[tid] = s_status[tid];
         P.rep_iters[tid] = s_iters[tid];
         P.rep_outer[tid] = s_outer[tid];
         P.rep_rel[tid] = s_rel[tid];
     }
+}
+
+// One system: CTA b of the grid is CTA b of the system.
+template <typename TM, int R>
+__global__ void __launch_bounds__(kThreads, 1) k_solve(SolveParams P) {
+    solve_body<TM, R>(P, blockIdx.x);
+}
+
+// Several independent systems in one cooperative launch: job j owns the CTAs
+// [cta0[j], cta0[j + 1]) and synchronises only among them (its own barrier
+// state, partials and reports).  A CTA copies its job's parameters into
+// shared memory once.
+template <typename TM, int R>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_solve_jobs(const SolveParams* __restrict__ jobs, const int* __restrict__ cta0, int n_jobs) {
+    __shared__ __align__(16) SolveParams sP;
+    __shared__ int s_job;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_jobs - 1;  // last job whose first CTA is <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (cta0[mid] <= (int)blockIdx.x) lo = mid;
+            else hi = mid - 1;
+        }
+        s_job = lo;
+    }
+    __syncthreads();
+    const int j = s_job;
+    static_assert(sizeof(SolveParams) % sizeof(int) == 0, "parameter block copied as ints");
+    const int* src = (const int*)(jobs + j);
+    int* dst = (int*)&sP;
+    for (int i = threadIdx.x; i < (int)(sizeof(SolveParams) / sizeof(int)); i += kThreads) dst[i] = src[i];
+    __syncthreads();
+    solve_body<TM, R>(sP, (int)blockIdx.x - cta0[j]);
 }
 
 // ---------------------------------------------------------------------------
@@ -842,28 +884,45 @@ static int pick_tile(int nrhs, int requested) {
     return R;
 }
 
-// Solves tile by tile; b and x are device arrays [n_dof][nrhs].
-static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d_b, double2* d_x,
-                              bool use_x0, const fe_solve_opts& o, fe_solve_report* rep) {
-    const fe_mesh* m = s->mesh;
-    cudaStream_t st = ctx->stream;
-    const int64_t n_dof = 3 * (int64_t)m->n_act;
-    const int R = pick_tile(nrhs, o.rhs_tile);
-    const bool fp64 = o.precision == FE_PREC_FP64;
-    if (!fp64 && !s->val32.ptr) {
-        set_error("mixed-precision solve of a system assembled in FP64 only");
+static void free_workspace(cudaStream_t st, Workspace& w) {
+    for (DevBuf* b : {&w.b, &w.x, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.pM, &w.w, &w.partial, &w.result, &w.sync, &w.rep,
+                      &w.trace})
+        dev_free(st, *b);
+}
+
+// Krylov workspace of one tile of R columns for up to max_cta CTAs.
+// Bytes of one inner-precision vector entry (uM, pM, w): complex128,
+// complex64 or a complex FP32 pair.
+static size_t inner_bytes(int prec) { return prec == FE_PREC_MIXED ? sizeof(float2) : sizeof(double2); }
+
+// Inner-precision matrix planes of a system, or NULL when it was not
+// assembled for that precision.
+static const void* inner_matrix(const fe_system* s, int prec) {
+    return prec == FE_PREC_FP64 ? s->val64.ptr : (prec == FE_PREC_MIXED ? s->val32.ptr : s->valdf.ptr);
+}
+
+static fe_status check_system_precision(const fe_system* s, int prec, const char* who) {
+    if (!inner_matrix(s, prec)) {
+        set_error("%s: the system was not assembled for precision %d (assemble with that precision)", who, prec);
         return FE_ERR_INVALID_ARG;
     }
-    const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);  // inner-precision vectors (uM, w)
-    Workspace w;
-    auto cleanup = [&]() {
-        for (DevBuf* b : {&w.b, &w.x, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.pM, &w.w, &w.partial, &w.result, &w.sync,
-                          &w.rep, &w.trace})
-            dev_free(st, *b);
-    };
-    fe_status e = FE_OK;
+    return FE_OK;
+}
+
+template <typename F>
+static fe_status with_inner_type(int prec, F&& f) {
+    switch (prec) {
+        case FE_PREC_FP64: return f((double*)nullptr);
+        case FE_PREC_MIXED: return f((float*)nullptr);
+        case FE_PREC_DF: return f((DFloat*)nullptr);
+        default: set_error("unknown precision %d", prec); return FE_ERR_INVALID_ARG;
+    }
+}
+
+static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec, int max_cta, Workspace& w) {
+    const bool fp64 = prec == FE_PREC_FP64;
+    const size_t esz = inner_bytes(prec);  // inner-precision vectors (uM, w)
     const size_t nv = (size_t)n_dof * R;
-    const int max_cta = 2 * ctx->num_sms;
     for (auto pr : {std::make_pair(&w.b, nv * sizeof(double2)), std::make_pair(&w.x, nv * sizeof(double2)),
                     std::make_pair(&w.r, nv * sizeof(double2)), std::make_pair(&w.u, nv * sizeof(double2)),
                     std::make_pair(&w.p, nv * sizeof(double2)), std::make_pair(&w.s, nv * sizeof(double2)),
@@ -873,11 +932,93 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
                     std::make_pair(&w.result, (size_t)kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.sync, sizeof(SyncState)),
                     std::make_pair(&w.rep, (size_t)R * (3 * sizeof(int) + sizeof(double)) + 64)}) {
-        if ((e = dev_alloc(st, *pr.first, pr.second)) != FE_OK) {
-            cleanup();
+        const fe_status e = dev_alloc(st, *pr.first, pr.second);
+        if (e != FE_OK) {
+            free_workspace(st, w);
             return e;
         }
     }
+    return FE_OK;
+}
+
+// Bytes alloc_workspace takes (before allocator rounding).
+size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta) {
+    const bool fp64 = prec == FE_PREC_FP64;
+    const size_t nv = (size_t)n_dof * R;
+    const size_t esz = inner_bytes(prec);
+    return nv * (6 * sizeof(double2) + (fp64 ? 1 : 3) * esz) + (size_t)(max_cta + 1) * kMaxNV * R * sizeof(double) +
+           (size_t)R * 32 + 4096;
+}
+
+// Solve parameters for a tile of R columns held in workspace w (n_cta and the
+// shared-memory layout are set at launch).
+static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, int R, int prec,
+                        const fe_solve_opts& o, bool use_x0) {
+    const fe_mesh* m = s->mesh;
+    const bool fp64 = prec == FE_PREC_FP64;
+    const bool df = prec == FE_PREC_DF;
+    P = SolveParams{};
+    P.n_rows = m->n_act;
+    P.rp = (const int*)m->row_ptr.ptr;
+    P.col = (const int*)m->col_idx.ptr;
+    P.val64 = (const double2*)s->val64.ptr;
+    P.valM = inner_matrix(s, prec);
+    P.stride = s->stride;
+    P.dinv64 = (const double2*)s->dinv64.ptr;
+    // class stencils and cost-balanced product ranges pay off for the
+    // complex64 and FP32-pair products; the FP64 products stay explicit and
+    // uniform
+    const bool classes = !fp64 && !(df && getenv("FE_DF_NOCLASS"));
+    P.row_class = classes ? (const signed char*)s->row_class.ptr : nullptr;
+    P.stencil = (const StencilSet*)s->stencil.ptr;
+    P.cost_prefix = classes ? (const int*)(df ? s->cost_prefix_alu.ptr : s->cost_prefix.ptr) : nullptr;
+    P.cost_total = classes ? (df ? s->cost_total_alu : s->cost_total) : (int64_t)m->n_act;
+    P.b = (const double2*)w.b.ptr;
+    P.x = (double2*)w.x.ptr;
+    P.r = (double2*)w.r.ptr;
+    P.u = (double2*)w.u.ptr;
+    P.p = (double2*)w.p.ptr;
+    P.s = (double2*)w.s.ptr;
+    P.uM = fp64 ? w.u.ptr : w.uM.ptr;
+    P.pM = fp64 ? w.p.ptr : w.pM.ptr;
+    P.w = w.w.ptr;
+    P.trace = (unsigned long long*)w.trace.ptr;
+    // lexicographic node ranks: a neighbour is at most one plane, one line
+    // and one node away
+    P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
+    P.sync = (SyncState*)w.sync.ptr;
+    P.partial = (double*)w.partial.ptr;
+    P.result = (double*)w.result.ptr;
+    P.tol = o.tol;
+    // complex64 passes restart at each refinement; FP64 and FP32-pair
+    // products are accurate enough to keep the directions across refreshes
+    P.reliable = prec == FE_PREC_MIXED ? o.reliable : 0.0;
+    P.restart = prec == FE_PREC_MIXED ? 1 : 0;
+    P.max_iter = o.max_iter;
+    P.max_outer = o.max_outer;
+    P.use_x0 = use_x0 ? 1 : 0;
+    int* ri = (int*)w.rep.ptr;
+    P.rep_status = ri;
+    P.rep_iters = ri + R;
+    P.rep_outer = ri + 2 * R;
+    P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
+    P.timeout_ns = 4000000000ull;
+    P.spin_ns = getenv("FE_SPIN_NS") ? (unsigned)atoi(getenv("FE_SPIN_NS")) : 0u;
+}
+
+// Solves tile by tile; b and x are device arrays [n_dof][nrhs].
+static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d_b, double2* d_x,
+                              bool use_x0, const fe_solve_opts& o, fe_solve_report* rep) {
+    const fe_mesh* m = s->mesh;
+    cudaStream_t st = ctx->stream;
+    const int64_t n_dof = 3 * (int64_t)m->n_act;
+    const int R = pick_tile(nrhs, o.rhs_tile);
+    const int prec = o.precision;
+    FE_TRY(check_system_precision(s, prec, "solve"));
+    Workspace w;
+    auto cleanup = [&]() { free_workspace(st, w); };
+    fe_status e = alloc_workspace(st, n_dof, R, prec, 2 * ctx->num_sms, w);
+    if (e != FE_OK) return e;
     const bool tracing = getenv("FE_TRACE") && getenv("FE_TRACE")[0] == '1';
     const size_t trace_bytes = (size_t)ctx->num_sms * kTraceIters * kTracePhases * sizeof(unsigned long long);
     if (tracing && (e = dev_alloc(st, w.trace, trace_bytes)) != FE_OK) {
@@ -899,50 +1040,10 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
             count_launches(1);
         }
         cudaMemsetAsync(w.sync.ptr, 0, sizeof(SyncState), st);
-        SolveParams P{};
-        P.n_rows = m->n_act;
-        P.rp = (const int*)m->row_ptr.ptr;
-        P.col = (const int*)m->col_idx.ptr;
-        P.val64 = (const double2*)s->val64.ptr;
-        P.valM = fp64 ? s->val64.ptr : s->val32.ptr;
-        P.stride = s->stride;
-        P.dinv64 = (const double2*)s->dinv64.ptr;
-        // class stencils and cost-balanced product ranges pay off for the
-        // complex64 products; the FP64 products stay explicit and uniform
-        P.row_class = fp64 ? nullptr : (const signed char*)s->row_class.ptr;
-        P.stencil = (const StencilSet*)s->stencil.ptr;
-        P.cost_prefix = fp64 ? nullptr : (const int*)s->cost_prefix.ptr;
-        P.cost_total = fp64 ? (int64_t)m->n_act : s->cost_total;
-        P.b = (const double2*)w.b.ptr;
-        P.x = (double2*)w.x.ptr;
-        P.r = (double2*)w.r.ptr;
-        P.u = (double2*)w.u.ptr;
-        P.p = (double2*)w.p.ptr;
-        P.s = (double2*)w.s.ptr;
-        P.uM = fp64 ? w.u.ptr : w.uM.ptr;
-        P.pM = fp64 ? w.p.ptr : w.pM.ptr;
-        P.w = w.w.ptr;
-        P.trace = (unsigned long long*)w.trace.ptr;
-        // lexicographic node ranks: a neighbour is at most one plane, one
-        // line and one node away
-        P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
-        P.sync = (SyncState*)w.sync.ptr;
-        P.partial = (double*)w.partial.ptr;
-        P.result = (double*)w.result.ptr;
-        P.tol = o.tol;
-        P.reliable = fp64 ? 0.0 : o.reliable;
-        P.restart = fp64 ? 0 : 1;
-        P.max_iter = o.max_iter;
-        P.max_outer = o.max_outer;
-        P.use_x0 = use_x0 ? 1 : 0;
-        int* ri = (int*)w.rep.ptr;
-        P.rep_status = ri;
-        P.rep_iters = ri + R;
-        P.rep_outer = ri + 2 * R;
-        P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
-        P.timeout_ns = 4000000000ull;
-        P.spin_ns = getenv("FE_SPIN_NS") ? (unsigned)atoi(getenv("FE_SPIN_NS")) : 0u;
-        e = fp64 ? dispatch<double>(ctx, R, P) : dispatch<float>(ctx, R, P);
+        SolveParams P;
+        fill_params(P, s, w, R, prec, o, use_x0);
+        int* ri = P.rep_status;
+        e = with_inner_type(prec, [&](auto* tag) { return dispatch<std::remove_pointer_t<decltype(tag)>>(ctx, R, P); });
         if (e != FE_OK) break;
         const unsigned gs = (unsigned)((n_dof * nc + 255) / 256);
         k_scatter_cols<<<gs, 256, 0, st>>>((const double2*)w.x.ptr, R, nc, d_x, nrhs, c0, n_dof);
@@ -1003,6 +1104,205 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
 }
 
 // ---------------------------------------------------------------------------
+// Jobs: independent solves that share one cooperative launch.  A job is one
+// system with up to 32 right-hand sides, padded to a power-of-two tile width
+// with zero columns (a zero right-hand side is converged at its first
+// residual).  The server packs jobs of one width and precision into a launch.
+// ---------------------------------------------------------------------------
+struct SolveJob {
+    const fe_system* sys = nullptr;
+    int nrhs = 0, R = 1;
+    int prec = FE_PREC_FP64;
+    int64_t n_dof = 0;
+    Workspace w;
+    SolveParams P{};
+};
+
+fe_status job_create(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d_b, const fe_solve_opts& o,
+                     SolveJob** out) {
+    *out = nullptr;
+    if (nrhs < 1 || nrhs > 32) {
+        set_error("job: nrhs %d outside 1..32", nrhs);
+        return FE_ERR_INVALID_ARG;
+    }
+    const int prec = o.precision;
+    FE_TRY(check_system_precision(s, prec, "job"));
+    SolveJob* j = new (std::nothrow) SolveJob();
+    if (!j) {
+        set_error("job: host allocation failed");
+        return FE_ERR_OOM;
+    }
+    j->sys = s;
+    j->nrhs = nrhs;
+    j->R = pick_tile(nrhs, 0);
+    j->prec = prec;
+    j->n_dof = 3 * (int64_t)s->mesh->n_act;
+    cudaStream_t st = ctx->stream;
+    fe_status e = alloc_workspace(st, j->n_dof, j->R, prec, ctx->num_sms, j->w);
+    if (e != FE_OK) {
+        delete j;
+        return e;
+    }
+    const unsigned gb = (unsigned)((j->n_dof * j->R + 255) / 256);
+    k_gather_cols<<<gb, 256, 0, st>>>(d_b, nrhs, 0, nrhs, (double2*)j->w.b.ptr, j->R, j->n_dof);
+    count_launches(1);
+    fill_params(j->P, s, j->w, j->R, prec, o, false);
+    *out = j;
+    return FE_OK;
+}
+
+int job_width(const SolveJob* j) { return j->R; }
+int64_t job_rows(const SolveJob* j) { return j->P.n_rows; }
+
+void job_destroy(fe_ctx* ctx, SolveJob* j) {
+    if (!j) return;
+    free_workspace(ctx->stream, j->w);
+    delete j;
+}
+
+template <typename T, int R>
+static fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n) {
+    using C = typename CplxT<T>::type;
+    std::vector<SolveParams> Ps(n);
+    std::vector<int> cta0(n + 1, 0);
+    const int red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
+    const int col_bytes = R == 1 ? (int)(kWarps * kColsPerWarp * sizeof(int)) : 0;
+    size_t dyn = (size_t)red_bytes + col_bytes;
+    for (int i = 0; i < n; ++i) {
+        SolveParams& P = Ps[i];
+        P = jobs[i]->P;
+        P.n_cta = n_cta[i];
+        P.red_bytes = red_bytes;
+        P.col_bytes = col_bytes;
+        const int64_t rows_per_cta = std::min<int64_t>(P.n_rows, P.cost_total / P.n_cta + 9);
+        const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
+        const size_t need = (size_t)red_bytes + col_bytes + (size_t)halo_bytes;
+        P.stage = (P.halo > 0 && need <= kSmemBudget) ? 1 : 0;
+        if (P.stage) dyn = std::max(dyn, need);
+        cta0[i + 1] = cta0[i] + n_cta[i];
+        FE_CUDA(cudaMemsetAsync(P.sync, 0, sizeof(SyncState), ctx->stream));
+    }
+    const int grid = cta0[n];
+    DevBuf dparams, dcta;
+    FE_TRY(dev_alloc(ctx->stream, dparams, (size_t)n * sizeof(SolveParams)));
+    fe_status e = dev_alloc(ctx->stream, dcta, (size_t)(n + 1) * sizeof(int));
+    if (e != FE_OK) {
+        dev_free(ctx->stream, dparams);
+        return e;
+    }
+    auto done = [&](fe_status st) {
+        dev_free(ctx->stream, dparams);
+        dev_free(ctx->stream, dcta);
+        return st;
+    };
+    if (cudaMemcpyAsync(dparams.ptr, Ps.data(), (size_t)n * sizeof(SolveParams), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess ||
+        cudaMemcpyAsync(dcta.ptr, cta0.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                        ctx->stream) != cudaSuccess) {
+        set_error("jobs: parameter upload failed");
+        return done(FE_ERR_CUDA);
+    }
+    if (cudaFuncSetAttribute((const void*)k_solve_jobs<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)dyn) != cudaSuccess) {
+        set_error("jobs: shared-memory attribute rejected");
+        return done(FE_ERR_CUDA);
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve_jobs<T, R>, kThreads, dyn);
+    if (per_sm < 1 || grid > per_sm * ctx->num_sms) {
+        set_error("jobs: %d CTAs do not fit on the device at once", grid);
+        return done(FE_ERR_INVALID_ARG);
+    }
+    const SolveParams* pp = (const SolveParams*)dparams.ptr;
+    const int* pc = (const int*)dcta.ptr;
+    void* args[] = {(void*)&pp, (void*)&pc, (void*)&n};
+    cudaEventRecord(ctx->ev0, ctx->stream);
+    const cudaError_t le = cudaLaunchCooperativeKernel((void*)k_solve_jobs<T, R>, dim3(grid), dim3(kThreads), args,
+                                                       dyn, ctx->stream);
+    if (le != cudaSuccess) {
+        set_error("jobs: launch failed: %s", cudaGetErrorString(le));
+        return done(FE_ERR_CUDA);
+    }
+    cudaEventRecord(ctx->ev1, ctx->stream);
+    count_launches(1);
+    return done(FE_OK);
+}
+
+template <typename T>
+static fe_status launch_jobs_w(fe_ctx* ctx, int R, SolveJob* const* jobs, const int* n_cta, int n) {
+    switch (R) {
+        case 1: return launch_jobs_t<T, 1>(ctx, jobs, n_cta, n);
+        case 2: return launch_jobs_t<T, 2>(ctx, jobs, n_cta, n);
+        case 4: return launch_jobs_t<T, 4>(ctx, jobs, n_cta, n);
+        case 8: return launch_jobs_t<T, 8>(ctx, jobs, n_cta, n);
+        case 16: return launch_jobs_t<T, 16>(ctx, jobs, n_cta, n);
+        case 32: return launch_jobs_t<T, 32>(ctx, jobs, n_cta, n);
+        default: set_error("jobs: unsupported tile width %d", R); return FE_ERR_UNSUPPORTED;
+    }
+}
+
+// Enqueues one cooperative launch of n jobs of one width and precision; job i
+// gets n_cta[i] CTAs (1..its row count).
+fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n) {
+    if (n < 1) return FE_OK;
+    const int R = jobs[0]->R;
+    const int prec = jobs[0]->prec;
+    int64_t total = 0;
+    for (int i = 0; i < n; ++i) {
+        if (jobs[i]->R != R || jobs[i]->prec != prec) {
+            set_error("jobs: one launch takes one tile width and one precision");
+            return FE_ERR_INVALID_ARG;
+        }
+        if (n_cta[i] < 1 || n_cta[i] > std::max(1, jobs[i]->P.n_rows)) {
+            set_error("jobs: job %d asks for %d CTAs", i, n_cta[i]);
+            return FE_ERR_INVALID_ARG;
+        }
+        total += n_cta[i];
+    }
+    if (total > ctx->num_sms) {
+        set_error("jobs: %lld CTAs exceed one per SM", (long long)total);
+        return FE_ERR_INVALID_ARG;
+    }
+    return with_inner_type(prec, [&](auto* tag) {
+        return launch_jobs_w<std::remove_pointer_t<decltype(tag)>>(ctx, R, jobs, n_cta, n);
+    });
+}
+
+// Copies a finished job's solution (the nrhs real columns, [n_dof][nrhs]) and
+// reports to the host; waits for the context's stream.
+fe_status job_collect(fe_ctx* ctx, SolveJob* j, fe_complex* x_host, fe_solve_report* rep) {
+    cudaStream_t st = ctx->stream;
+    const int R = j->R;
+    std::vector<int> ri(3 * R);
+    std::vector<double> rd(R);
+    SyncState hs{};
+    if (x_host)
+        FE_CUDA(cudaMemcpy2DAsync(x_host, (size_t)j->nrhs * sizeof(double2), j->w.x.ptr, (size_t)R * sizeof(double2),
+                                  (size_t)j->nrhs * sizeof(double2), (size_t)j->n_dof, cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaMemcpyAsync(ri.data(), j->P.rep_status, 3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaMemcpyAsync(rd.data(), j->P.rep_rel, R * sizeof(double), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaMemcpyAsync(&hs, j->P.sync, sizeof(SyncState), cudaMemcpyDeviceToHost, st));
+    FE_CUDA(cudaStreamSynchronize(st));
+    fe_status worst = FE_OK;
+    for (int c = 0; c < j->nrhs; ++c) {
+        if (rep) {
+            rep[c].status = ri[c];
+            rep[c].iterations = ri[R + c];
+            rep[c].outer = ri[2 * R + c];
+            rep[c].reserved = 0;
+            rep[c].rel_residual = rd[c];
+        }
+        if (ri[c] != FE_OK && worst == FE_OK) worst = (fe_status)ri[c];
+    }
+    if (hs.err) {
+        set_error("job: a barrier wait expired (device status %d)", hs.err);
+        return FE_ERR_TIMEOUT;
+    }
+    if (worst != FE_OK) set_error("job: at least one right-hand side did not reach the tolerance");
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
 // Fixed scratch for callers that cannot allocate device memory.
 //
 // fe_solve_rhs_noalloc keeps its whole workspace (Krylov vectors, reduction
@@ -1039,8 +1339,8 @@ static fe_status static_scratch(int device, char** out) {
 static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
     fe_solve_opts_default(&out);
     if (o) out = *o;
-    if (out.precision != FE_PREC_FP64 && out.precision != FE_PREC_MIXED) {
-        set_error("solve: precision must be FP64 or MIXED");
+    if (out.precision != FE_PREC_FP64 && out.precision != FE_PREC_MIXED && out.precision != FE_PREC_DF) {
+        set_error("solve: precision must be FP64, MIXED or DF");
         return FE_ERR_INVALID_ARG;
     }
     if (!(out.tol > 0.0) || out.max_iter < 1 || out.max_outer < 1 || !(out.reliable >= 0.0 && out.reliable < 1.0) || out.rhs_tile < 0) {
@@ -1097,6 +1397,14 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
             k_spmv_cols<float2><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
                 (const float2*)s->val32.ptr, s->stride, col, rp, (const float2*)x, (float2*)y, m->n_act, nrhs);
         }
+    } else if (precision == FE_PREC_DF) {
+        if (!s->valdf.ptr) {
+            set_error("fe_spmv: no FP32-pair copy (system not assembled with FE_PREC_DF)");
+            return FE_ERR_INVALID_ARG;
+        }
+        const int64_t n = (int64_t)m->n_act * nrhs;  // one thread per (row, column), also for nrhs = 1
+        k_spmv_cols<float4><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+            (const float4*)s->valdf.ptr, s->stride, col, rp, (const float4*)x, (float4*)y, m->n_act, nrhs);
     } else {
         set_error("fe_spmv: bad precision");
         return FE_ERR_INVALID_ARG;
@@ -1187,38 +1495,43 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     }
     fe_solve_opts opt;
     FE_TRY(check_opts(o, opt));
-    const bool fp64 = opt.precision == FE_PREC_FP64;
-    if (!fp64 && !s->val32.ptr) {
-        set_error("fe_solve_rhs_noalloc: mixed-precision solve of a system assembled in FP64 only");
-        return FE_ERR_INVALID_ARG;
-    }
+    const int prec = opt.precision;
+    FE_TRY(check_system_precision(s, prec, "fe_solve_rhs_noalloc"));
     FE_CUDA(cudaSetDevice(ctx->device));
     char* base = nullptr;
     FE_TRY(static_scratch(ctx->device, &base));
     const fe_mesh* m = s->mesh;
     const int R = nrhs;
     const size_t nv = (size_t)3 * m->n_act * R;
-    const size_t esz = fp64 ? sizeof(double2) : sizeof(float2);
+    const size_t esz = inner_bytes(prec);
     const int max_cta = 2 * ctx->num_sms;
-    // carve the workspace, 256-byte aligned pieces
+    // carve the workspace out of the static array, 256-byte aligned pieces;
+    // b and x are the caller's buffers
     size_t off = 0;
-    auto take = [&](size_t bytes) {
-        char* p = base + off;
+    auto take = [&](DevBuf& b, size_t bytes) {
+        b.ptr = base + off;
+        b.bytes = bytes;
         off += (bytes + 255) & ~(size_t)255;
-        return p;
     };
-    double2* r = (double2*)take(nv * sizeof(double2));
-    double2* u = (double2*)take(nv * sizeof(double2));
-    double2* pv = (double2*)take(nv * sizeof(double2));
-    double2* sv = (double2*)take(nv * sizeof(double2));
-    void* w = take(nv * esz);
-    void* uM = fp64 ? (void*)u : take(nv * esz);
-    void* pM = fp64 ? (void*)pv : take(nv * esz);
-    double* partial = (double*)take((size_t)max_cta * kMaxNV * R * sizeof(double));
-    double* result = (double*)take((size_t)kMaxNV * R * sizeof(double));
-    SyncState* sync = (SyncState*)take(sizeof(SyncState));
-    int* ri = (int*)take((size_t)3 * R * sizeof(int));
-    double* rrel = (double*)take((size_t)R * sizeof(double));
+    Workspace w;
+    w.b.ptr = const_cast<void*>(b_dev);
+    w.x.ptr = x_dev;
+    take(w.r, nv * sizeof(double2));
+    take(w.u, nv * sizeof(double2));
+    take(w.p, nv * sizeof(double2));
+    take(w.s, nv * sizeof(double2));
+    take(w.w, nv * esz);
+    if (prec == FE_PREC_FP64) {
+        w.uM = w.u;
+        w.pM = w.p;
+    } else {
+        take(w.uM, nv * esz);
+        take(w.pM, nv * esz);
+    }
+    take(w.partial, (size_t)max_cta * kMaxNV * R * sizeof(double));
+    take(w.result, (size_t)kMaxNV * R * sizeof(double));
+    take(w.sync, sizeof(SyncState));
+    take(w.rep, (size_t)R * (3 * sizeof(int) + sizeof(double)) + 64);
     if (off > kStaticScratchBytes) {
         set_error("fe_solve_rhs_noalloc: needs %zu bytes of scratch, the static array holds %zu (n_dof x nrhs too "
                   "large)",
@@ -1226,47 +1539,15 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
         return FE_ERR_INVALID_ARG;
     }
     cudaStream_t st = ctx->stream;
-    FE_CUDA(cudaMemsetAsync(sync, 0, sizeof(SyncState), st));  // the array keeps the previous call's contents
-    SolveParams P{};
-    P.n_rows = m->n_act;
-    P.rp = (const int*)m->row_ptr.ptr;
-    P.col = (const int*)m->col_idx.ptr;
-    P.val64 = (const double2*)s->val64.ptr;
-    P.valM = fp64 ? s->val64.ptr : s->val32.ptr;
-    P.stride = s->stride;
-    P.dinv64 = (const double2*)s->dinv64.ptr;
-    P.row_class = fp64 ? nullptr : (const signed char*)s->row_class.ptr;
-    P.stencil = (const StencilSet*)s->stencil.ptr;
-    P.cost_prefix = fp64 ? nullptr : (const int*)s->cost_prefix.ptr;
-    P.cost_total = fp64 ? (int64_t)m->n_act : s->cost_total;
-    P.b = (const double2*)b_dev;
-    P.x = (double2*)x_dev;
-    P.r = r;
-    P.u = u;
-    P.p = pv;
-    P.s = sv;
-    P.uM = uM;
-    P.pM = pM;
-    P.w = w;
-    P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
-    P.sync = sync;
-    P.partial = partial;
-    P.result = result;
-    P.tol = opt.tol;
-    P.reliable = fp64 ? 0.0 : opt.reliable;
-    P.restart = fp64 ? 0 : 1;
-    P.max_iter = opt.max_iter;
-    P.max_outer = opt.max_outer;
-    P.use_x0 = use_x0 ? 1 : 0;
-    P.rep_status = ri;
-    P.rep_iters = ri + R;
-    P.rep_outer = ri + 2 * R;
-    P.rep_rel = rrel;
+    FE_CUDA(cudaMemsetAsync(w.sync.ptr, 0, sizeof(SyncState), st));  // the array keeps the previous call's contents
+    SolveParams P;
+    fill_params(P, s, w, R, prec, opt, use_x0 != 0);
     P.trace = nullptr;
-    P.timeout_ns = 4000000000ull;
-    P.spin_ns = 0;
+    SyncState* sync = P.sync;
+    int* ri = P.rep_status;
+    double* rrel = P.rep_rel;
     ctx->last_solve = fe_solve_stats{};
-    FE_TRY(fp64 ? dispatch<double>(ctx, R, P) : dispatch<float>(ctx, R, P));
+    FE_TRY(with_inner_type(prec, [&](auto* tag) { return dispatch<std::remove_pointer_t<decltype(tag)>>(ctx, R, P); }));
     SyncState hs{};
     int h_ri[3 * 32];
     double h_rel[32];

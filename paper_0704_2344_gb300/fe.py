@@ -24,7 +24,7 @@ FE_ERR_CUDA = -7
 FE_ERR_UNSUPPORTED = -8
 
 FE_VARIANT_S, FE_VARIANT_L, FE_VARIANT_P = 0, 1, 2
-FE_PREC_FP64, FE_PREC_MIXED = 0, 1
+FE_PREC_FP64, FE_PREC_MIXED, FE_PREC_DF = 0, 1, 2
 
 LIB_PATH = Path(__file__).resolve().parent / "libfe_gb300.so"
 
@@ -55,6 +55,12 @@ class fe_mesh_stats(C.Structure):
                                           "n_dof", "nnzb", "n_faces_ext", "n_faces_pec", "device_bytes")]
 
 
+class fe_system_stats(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("reserved", C.c_int32)] + [
+        (n, C.c_int64) for n in ("n_rows", "nnzb", "rows_general", "rows_diagonal", "blocks_explicit",
+                                 "device_bytes")]
+
+
 class fe_planewave(C.Structure):
     _fields_ = [("k_hat", C.c_double * 3), ("p_hat", C.c_double * 3), ("amplitude", fe_complex)]
 
@@ -72,6 +78,30 @@ class fe_solve_stats(C.Structure):
 class fe_solve_report(C.Structure):
     _fields_ = [("status", C.c_int32), ("iterations", C.c_int32), ("outer", C.c_int32),
                 ("reserved", C.c_int32), ("rel_residual", C.c_double)]
+
+
+class fe_serve_opts(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
+                ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("hbm_budget", C.c_int64),
+                ("max_ctas", C.c_int32), ("work_per_cta", C.c_int32)]
+
+
+class fe_request(C.Structure):
+    _fields_ = [("mesh", fe_mesh_desc), ("freq_hz", C.c_double), ("nrhs", C.c_int32),
+                ("waves", C.POINTER(fe_planewave))]
+
+
+class fe_result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("nrhs", C.c_int32), ("n_dof", C.c_int64),
+                ("x", C.POINTER(fe_complex)), ("node_id", C.POINTER(C.c_int32)),
+                ("reports", C.POINTER(fe_solve_report)), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double), ("batch_jobs", C.c_int32), ("batch_ctas", C.c_int32),
+                ("message", C.c_char_p)]
+
+
+class fe_serve_stats(C.Structure):
+    _fields_ = [(n, C.c_int64) for n in ("submitted", "completed", "failed", "launches", "jobs_launched",
+                                         "budget_bytes", "peak_admitted_bytes")] + [("solve_device_s", C.c_double)]
 
 
 _lib = None
@@ -97,6 +127,8 @@ def load() -> C.CDLL:
         "fe_mesh_destroy": (None, [P]),
         "fe_assemble": (C.c_int, [P, P, C.c_double, C.c_int32, C.POINTER(P)]),
         "fe_system_export": (C.c_int, [P, P, P, P, P]),
+        "fe_system_export_df": (C.c_int, [P, P, P]),
+        "fe_system_info": (C.c_int, [P, C.POINTER(fe_system_stats)]),
         "fe_system_destroy": (None, [P]),
         "fe_rhs": (C.c_int, [P, P, C.c_int32, C.POINTER(fe_planewave), P, C.c_int32]),
         "fe_spmv": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P]),
@@ -108,6 +140,16 @@ def load() -> C.CDLL:
         "fe_last_solve_stats": (C.c_int, [P, C.POINTER(fe_solve_stats)]),
         "fe_solve_rhs_noalloc": (C.c_int, [P, P, C.c_int32, P, P, C.c_int32, C.POINTER(fe_solve_opts),
                                            C.POINTER(fe_solve_report)]),
+        "fe_serve_opts_default": (None, [C.POINTER(fe_serve_opts)]),
+        "fe_serve_create": (C.c_int, [P, C.POINTER(fe_serve_opts), C.POINTER(P)]),
+        "fe_serve_submit": (C.c_int, [P, C.POINTER(fe_request), C.POINTER(C.c_uint64)]),
+        "fe_serve_poll": (C.c_int, [P, C.c_uint64, C.POINTER(fe_result)]),
+        "fe_serve_wait": (C.c_int, [P, C.c_uint64, C.c_double, C.POINTER(fe_result)]),
+        "fe_serve_release": (C.c_int, [P, C.c_uint64]),
+        "fe_serve_info": (C.c_int, [P, C.POINTER(fe_serve_stats)]),
+        "fe_serve_destroy": (None, [P]),
+        "fe_serve_plan": (C.c_int32, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int32,
+                                      C.c_int32, C.POINTER(C.c_int32)]),
         "fe_last_error": (C.c_char_p, []),
         "fe_launch_count": (C.c_int64, []),
     }
@@ -262,6 +304,21 @@ def fe_system_export(ctx, system, mesh, c128=True, c64=False, dinv=False) -> dic
     return out
 
 
+def fe_system_info(system) -> dict:
+    st = fe_system_stats()
+    _check(load().fe_system_info(system, C.byref(st)), "fe_system_info")
+    return {n: int(getattr(st, n)) for n, _ in fe_system_stats._fields_ if n != "reserved"}
+
+
+def fe_system_export_df(ctx, system, mesh) -> np.ndarray:
+    """FP32-pair values [nnzb, 3, 3, 4] float32 (re_hi, im_hi, re_lo, im_lo)
+    of a system assembled with FE_PREC_DF."""
+    info = fe_mesh_info(mesh)
+    a = np.empty((info["nnzb"], 3, 3, 4), np.float32)
+    _check(load().fe_system_export_df(ctx, system, _ptr(a)), "fe_system_export_df")
+    return a
+
+
 def fe_system_destroy(system):
     load().fe_system_destroy(system)
 
@@ -352,3 +409,105 @@ def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_op
                                      C.byref(opts), rep)
     _check(st, "fe_solve_rhs_noalloc", ok=(FE_OK,) if raise_on_fail else _SOLVE_OK)
     return st, _reports(rep)
+
+
+# --------------------------------------------------------------------------
+# Serving
+def serve_opts(precision=FE_PREC_FP64, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
+               hbm_budget=0, max_ctas=0, work_per_cta=0) -> fe_serve_opts:
+    o = fe_serve_opts()
+    load().fe_serve_opts_default(C.byref(o))
+    o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
+    o.max_iter, o.max_outer, o.hbm_budget = int(max_iter), int(max_outer), int(hbm_budget)
+    o.max_ctas = int(max_ctas)
+    if work_per_cta:
+        o.work_per_cta = int(work_per_cta)
+    return o
+
+
+def fe_serve_create(ctx, opts: fe_serve_opts | None = None):
+    out = P()
+    _check(load().fe_serve_create(ctx, C.byref(opts or serve_opts()), C.byref(out)), "fe_serve_create")
+    return out
+
+
+def fe_serve_submit(server, problem, waves) -> int:
+    """Submits a workloads.VoxelProblem with its PlaneWaves; returns the ticket.
+    The request is copied, so the arguments may be dropped afterwards."""
+    d = fe_mesh_desc()
+    d.nx, d.ny, d.nz = int(problem.nx), int(problem.ny), int(problem.nz)
+    d.h = (C.c_double * 3)(*[float(v) for v in problem.h])
+    d.origin = (C.c_double * 3)(*[float(v) for v in problem.origin])
+    mat = np.ascontiguousarray(problem.material, dtype=np.uint8)
+    d.material = mat.ctypes.data
+    d.material_on_device = 0
+    eps = np.ascontiguousarray(np.asarray(problem.eps_r, dtype=np.complex128))
+    mu = np.ascontiguousarray(np.asarray(problem.mu_r, dtype=np.complex128))
+    d.n_materials = eps.size
+    d.eps_r = eps.ctypes.data_as(C.POINTER(fe_complex))
+    d.mu_r = mu.ctypes.data_as(C.POINTER(fe_complex))
+    arr = planewave_array(waves)
+    r = fe_request()
+    r.mesh = d
+    r.freq_hz = float(problem.freq_hz)
+    r.nrhs = len(arr)
+    r.waves = C.cast(arr, C.POINTER(fe_planewave))
+    t = C.c_uint64()
+    _check(load().fe_serve_submit(server, C.byref(r), C.byref(t)), "fe_serve_submit")
+    return int(t.value)
+
+
+def _result_dict(res: fe_result, copy: bool) -> dict:
+    out = {"status": int(res.status), "nrhs": int(res.nrhs), "n_dof": int(res.n_dof),
+           "t_submit": float(res.t_submit), "t_admit": float(res.t_admit), "t_done": float(res.t_done),
+           "batch_jobs": int(res.batch_jobs), "batch_ctas": int(res.batch_ctas),
+           "message": (res.message or b"").decode(errors="replace"), "x": None, "node_id": None, "reports": None}
+    if copy and res.x:
+        n = res.n_dof * res.nrhs
+        flat = np.ctypeslib.as_array(C.cast(res.x, C.POINTER(C.c_double)), shape=(2 * n,)).copy()
+        out["x"] = flat.view(np.complex128).reshape(res.n_dof, res.nrhs)
+    if copy and res.node_id and res.n_dof:
+        out["node_id"] = np.ctypeslib.as_array(res.node_id, shape=(res.n_dof // 3,)).copy()
+    if copy and res.reports:
+        out["reports"] = _reports([res.reports[i] for i in range(res.nrhs)])
+    return out
+
+
+def fe_serve_poll(server, ticket: int, copy: bool = True):
+    """None while pending; else the finished request as a dict (arrays copied)."""
+    res = fe_result()
+    st = _check(load().fe_serve_poll(server, int(ticket), C.byref(res)), "fe_serve_poll", ok=(FE_OK, FE_PENDING))
+    return None if st == FE_PENDING else _result_dict(res, copy)
+
+
+def fe_serve_wait(server, ticket: int, timeout_s: float = 60.0, copy: bool = True):
+    res = fe_result()
+    st = _check(load().fe_serve_wait(server, int(ticket), float(timeout_s), C.byref(res)), "fe_serve_wait",
+                ok=(FE_OK, FE_PENDING))
+    return None if st == FE_PENDING else _result_dict(res, copy)
+
+
+def fe_serve_release(server, ticket: int):
+    return _check(load().fe_serve_release(server, int(ticket)), "fe_serve_release", ok=(FE_OK, FE_PENDING))
+
+
+def fe_serve_info(server) -> dict:
+    s = fe_serve_stats()
+    _check(load().fe_serve_info(server, C.byref(s)), "fe_serve_info")
+    return {n: (float(getattr(s, n)) if n == "solve_device_s" else int(getattr(s, n)))
+            for n, _ in fe_serve_stats._fields_}
+
+
+def fe_serve_destroy(server):
+    load().fe_serve_destroy(server)
+
+
+def fe_serve_plan(rows, widths, max_ctas: int, work_per_cta: int) -> tuple[int, np.ndarray]:
+    """The server's packing rule (host only): returns (taken, n_cta per request)."""
+    r = np.ascontiguousarray(rows, dtype=np.int64)
+    w = np.ascontiguousarray(widths, dtype=np.int32)
+    out = np.zeros(r.size, np.int32)
+    taken = load().fe_serve_plan(int(r.size), r.ctypes.data_as(C.POINTER(C.c_int64)),
+                                 w.ctypes.data_as(C.POINTER(C.c_int32)), int(max_ctas), int(work_per_cta),
+                                 out.ctypes.data_as(C.POINTER(C.c_int32)))
+    return int(taken), out

@@ -117,6 +117,35 @@ def _check_values(fe, ctx, prob, variant="S", A=None, maps=None):
     assert derr.max() <= 1e-10, derr.max()
 
 
+def _df_split(v):
+    """Exact FP32-pair split of float64 values: hi = RN32(v), lo = RN32(v - hi)."""
+    hi = v.astype(np.float32)
+    return hi, (v - hi.astype(np.float64)).astype(np.float32)
+
+
+@pytest.mark.parametrize("name", ["rand1", "config1"])
+def test_assembly_df_pairs(fe, ctx, name):
+    """The FP32-pair copy (FE_PREC_DF) is exactly the split of the complex128
+    values, and hi + lo recovers them to about 2^-48 relative."""
+    prob = SMALL[name]()
+    m = fe.fe_mesh_create_from(ctx, prob)
+    try:
+        s = fe.fe_assemble(ctx, m, prob.freq_hz, fe.FE_PREC_DF)
+        try:
+            g = fe.fe_system_export(ctx, s, m, c128=True)["c128"]
+            df = fe.fe_system_export_df(ctx, s, m)
+        finally:
+            fe.fe_system_destroy(s)
+    finally:
+        fe.fe_mesh_destroy(m)
+    rh, rl = _df_split(g.real)
+    ih, il = _df_split(g.imag)
+    for k, ref in enumerate((rh, ih, rl, il)):
+        assert np.array_equal(df[..., k], ref), k
+    back = (df[..., 0].astype(np.float64) + df[..., 2]) + 1j * (df[..., 1].astype(np.float64) + df[..., 3])
+    assert np.abs(back - g).max() <= 2.0 ** -47 * np.abs(g).max()
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_assembly_values_small(fe, ctx, name):
     _check_values(fe, ctx, SMALL[name]())
@@ -193,6 +222,38 @@ def test_spmv_config2(fe, ctx):
     _spmv_check(fe, ctx, W.config2()[0], 1, seed=3)
 
 
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_spmv_fp32_pairs(fe, ctx, nrhs):
+    """FE_PREC_DF product: FP32-pair matrix and vector, error-free product
+    and sum steps.  Its error is a few 2^-48 of sum |a_ij x_j| per entry; the
+    bound 1e-12 is far below what complex64 arithmetic reaches (4e-6)."""
+    torch = _torch()
+    prob = W.random_small_grid(5, n_max=8, n_pec_boxes=2)
+    maps = fem.mesh_maps(prob)
+    A = fem.assemble(prob, maps=maps)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((maps.n_dof, nrhs)) + 1j * rng.standard_normal((maps.n_dof, nrhs))
+    rh, rl = _df_split(x.real)
+    ih, il = _df_split(x.imag)
+    xp = np.ascontiguousarray(np.stack([rh, ih, rl, il], axis=-1))
+    m = fe.fe_mesh_create_from(ctx, prob)
+    s = fe.fe_assemble(ctx, m, prob.freq_hz, fe.FE_PREC_DF)
+    try:
+        xd = torch.from_numpy(xp).cuda()
+        yd = torch.empty_like(xd)
+        torch.cuda.synchronize()
+        fe.fe_spmv(ctx, s, fe.FE_PREC_DF, nrhs, xd, yd)
+        fe.fe_ctx_synchronize(ctx)
+        y = yd.cpu().numpy().astype(np.float64)
+    finally:
+        fe.fe_system_destroy(s)
+        fe.fe_mesh_destroy(m)
+    ydf = (y[..., 0] + y[..., 2]) + 1j * (y[..., 1] + y[..., 3])
+    ref = A @ x
+    bound = abs(A) @ np.abs(x)
+    assert np.all(np.abs(ydf - ref) <= 1e-12 * bound)
+
+
 def _solve(fe, ctx, prob, waves, precision, **kw):
     m = fe.fe_mesh_create_from(ctx, prob)
     s = fe.fe_assemble(ctx, m, prob.freq_hz, precision)
@@ -205,7 +266,7 @@ def _solve(fe, ctx, prob, waves, precision, **kw):
     return x, rep
 
 
-@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("precision", ["FP64", "MIXED", "DF"])
 @pytest.mark.parametrize("name", ["box2", "config1", "rand1", "rand2"])
 def test_solve_matches_direct(fe, ctx, name, precision):
     prob = SMALL[name]()
@@ -260,7 +321,7 @@ def test_mesh_errors(fe, ctx):
     assert e.value.status == fe.FE_ERR_MESH
 
 
-@pytest.mark.parametrize("precision", ["FP64", "MIXED"])
+@pytest.mark.parametrize("precision", ["FP64", "MIXED", "DF"])
 def test_solve_config2_full_size(fe, ctx, config2, precision):
     """The 3-wavelength cube at full size (88 998 unknowns) in the launch
     configuration the benchmark times: FP64 true residual <= 1e-8 with the

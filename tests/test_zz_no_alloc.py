@@ -23,7 +23,7 @@ from paper_0704_2344_gb300 import workloads as W
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("precision", ["MIXED", "FP64"])
+@pytest.mark.parametrize("precision", ["MIXED", "FP64", "DF"])
 def test_noalloc_solve_matches_allocating_solve(fe, ctx, precision):
     import torch
 
