@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--requests", type=int, default=128,
                     help="config5: requests in the serving stream (the full stream has 512)")
-    ap.add_argument("--serve-precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--serve-precision", default="df", choices=["df", "fp64", "mixed"])
     return ap.parse_args()
 
 
@@ -392,7 +392,7 @@ def run_serving(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     reqs = W.config5(n_requests=args.requests)[rank::world]
     ctx = fe.fe_ctx_create(local_rank)
-    prec = fe.FE_PREC_MIXED if args.serve_precision == "mixed" else fe.FE_PREC_FP64
+    prec = {"mixed": fe.FE_PREC_MIXED, "fp64": fe.FE_PREC_FP64, "df": fe.FE_PREC_DF}[args.serve_precision]
     n_solves = sum(q.waves.count for q in reqs)
     n_dof_total = sum(3 * int(np.prod(np.array(q.problem.material.shape) + 1)) for q in reqs)
 
@@ -466,7 +466,7 @@ def run_serving(args, rank, world, local_rank):
     line = {
         "metric": "RHS solves/s at 1e-8 rel. residual", "value": value, "unit": "solves/s",
         "n_gpus": world, "steps": 1, "warmup": len(small), "ms_per_step": round(1e3 * wall, 2),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128" if prec == fe.FE_PREC_FP64 else "c64+f64",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": {"fp64": "c128", "mixed": "c64+f64", "df": "f32x2+f64"}[args.serve_precision],
         "data": "synthetic",
         "config": {"workload": f"config5: serving stream of {args.requests} cubes 8^3..50^3 nodes, 1-16 plane waves",
                    "requests_per_rank": len(reqs), "rhs_per_rank": n_solves, "grid_dof_per_rank": n_dof_total,

@@ -224,7 +224,7 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
  * launch.
  * ---------------------------------------------------------------------- */
 typedef struct fe_solve_opts {
-    int32_t precision;   /* fe_precision; default FE_PREC_MIXED */
+    int32_t precision;   /* fe_precision; default FE_PREC_DF */
     double tol;          /* true FP64 relative residual target; default 1e-8 */
     double reliable;     /* mixed mode: each time the recursive residual has dropped by this factor since the
                             last FP64 pass, the FP64 true residual b - A x replaces it and the complex64
@@ -232,6 +232,9 @@ typedef struct fe_solve_opts {
     int32_t max_iter;    /* cap on Krylov iterations per right-hand side; default 20000 */
     int32_t max_outer;   /* cap on true-residual replacements per right-hand side; default 200 */
     int32_t rhs_tile;    /* right-hand sides per device pass, 0 = automatic */
+    int32_t max_pass_iter; /* mixed mode: a complex64 pass that has not dropped by `reliable` after this
+                              many iterations is replaced all the same (its recursion has stalled);
+                              0 = no cap; default 2000 */
 } fe_solve_opts;
 
 void fe_solve_opts_default(fe_solve_opts* o);
@@ -302,7 +305,7 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
  * Requests that arrive during a launch join the next one.
  * ---------------------------------------------------------------------- */
 typedef struct fe_serve_opts {
-    int32_t precision;     /* FE_PREC_FP64 (default), FE_PREC_MIXED or FE_PREC_DF, for every request */
+    int32_t precision;     /* FE_PREC_DF (default), FE_PREC_FP64 or FE_PREC_MIXED, for every request */
     double tol;            /* true relative residual target; default 1e-8 */
     double reliable;       /* FE_PREC_MIXED refinement trigger; default 1e-4 */
     int32_t max_iter;      /* default 20000 */

@@ -369,14 +369,16 @@ __global__ void k_class_counts(const signed char* __restrict__ cls, const Stenci
     }
 }
 
-// Per-row product cost with weights w_explicit, w_general, w_diagonal.
-__global__ void k_row_cost(const signed char* __restrict__ cls, const StencilSet* __restrict__ S, int n_act,
-                           int w0, int w1, int w2, int* __restrict__ cost) {
+// Per-row product cost: w_block per stored block of an explicit row,
+// w_general for a general-stencil row, w_diagonal for a diagonal-stencil row.
+__global__ void k_row_cost(const signed char* __restrict__ cls, const StencilSet* __restrict__ S,
+                           const int* __restrict__ row_ptr, int n_act, int w_block, int w_general, int w_diagonal,
+                           int* __restrict__ cost) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_act) return;
     const int c = cls[r];
     const int kind = c >= 0 ? S->kind[c] : 0;
-    cost[r] = kind == 2 ? w2 : (kind == 1 ? w1 : w0);
+    cost[r] = kind == 2 ? w_diagonal : (kind == 1 ? w_general : w_block * (row_ptr[r + 1] - row_ptr[r]));
 }
 
 static void system_free(fe_system* s) {
@@ -490,18 +492,19 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         k_class_stencil<<<kMaxClasses, 32, 0, st>>>((const double2*)s->val64.ptr, s->stride,
                                                     (const int*)m->row_ptr.ptr, d_rep, (StencilSet*)s->stencil.ptr);
         count_launches(1);
-        // product cost prefixes: memory weights (explicit 8, general stencil 4,
-        // real diagonal stencil 1) for the complex64 products, arithmetic
-        // weights (7, 6, 1) for the double-float products
-        const int weights[2][3] = {{8, 4, 1}, {7, 6, 1}};
+        // product cost prefixes, in units of one stored block of an explicit
+        // row: a general-stencil row costs 18 (complex64) or 31 (FP32 pairs)
+        // such blocks, a diagonal-stencil row 10 or 8 (per-CTA product times
+        // measured on GB300 and fitted to these three row kinds)
+        const int weights[2][3] = {{1, 18, 10}, {1, 31, 8}};
         DevBuf* bufs[2] = {&s->cost_prefix, &s->cost_prefix_alu};
         int* d_total = (int*)ctx->small.ptr + 24;
         for (int k = 0; k < 2; ++k) {
             if ((e = dev_alloc(st, *bufs[k], (size_t)(m->n_act + 1) * sizeof(int))) != FE_OK) return fail(e);
             int* cp = (int*)bufs[k]->ptr;
             k_row_cost<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
-                (const signed char*)s->row_class.ptr, (const StencilSet*)s->stencil.ptr, m->n_act, weights[k][0],
-                weights[k][1], weights[k][2], cp);
+                (const signed char*)s->row_class.ptr, (const StencilSet*)s->stencil.ptr, (const int*)m->row_ptr.ptr,
+                m->n_act, weights[k][0], weights[k][1], weights[k][2], cp);
             count_launches(1);
             if ((e = scan_exclusive(st, cp, cp, m->n_act, d_total + k, ctx->scan_tmp)) != FE_OK) return fail(e);
             cudaMemcpyAsync(cp + m->n_act, d_total + k, sizeof(int), cudaMemcpyDeviceToDevice, st);
@@ -521,6 +524,11 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         }
         s->cost_total = ctx->h_small[24];
         s->cost_total_alu = ctx->h_small[25];
+        // bounds of one row's cost (an explicit row has 8 to 27 blocks)
+        for (int k = 0; k < 2; ++k) {
+            s->cost_min[k] = std::min({8 * weights[k][0], weights[k][1], weights[k][2]});
+            s->cost_max[k] = std::max({27 * weights[k][0], weights[k][1], weights[k][2]});
+        }
         const unsigned long long* hc = (const unsigned long long*)(ctx->h_small + 32);
         s->rows_general = (int64_t)hc[0];
         s->rows_diagonal = (int64_t)hc[1];

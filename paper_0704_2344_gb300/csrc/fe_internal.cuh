@@ -108,15 +108,15 @@ struct fe_system {
     // the products read them from a per-class stencil instead of the planes.
     fe::DevBuf row_class;            // int8 [n_act]: class (material < kMaxClasses) or -1
     fe::DevBuf stencil;              // StencilSet (device)
-    // prefix sum of a per-row cost of the sparse product (explicit row 8,
-    // regular row with a general stencil 4, real diagonal stencil 1): the
-    // product phases split rows across CTAs by equal cost
+    // prefix sum of a per-row cost of the complex64 sparse product (see
+    // fe_assemble for the weights): the product phases split rows across
+    // CTAs by equal cost
     fe::DevBuf cost_prefix;          // int [n_act + 1]
     int64_t cost_total = 0;
-    // the same with arithmetic weights (explicit 7, general stencil 6, real
-    // diagonal stencil 1) for the ALU-bound double-float products
+    // the same with the weights of the FP32-pair products
     fe::DevBuf cost_prefix_alu;      // int [n_act + 1]
     int64_t cost_total_alu = 0;
+    int cost_min[2] = {1, 1}, cost_max[2] = {1, 1};  // bounds of one row's cost (complex64, FP32 pairs)
     int64_t rows_general = 0, rows_diagonal = 0, blocks_explicit = 0;  // rows per product path
 };
 

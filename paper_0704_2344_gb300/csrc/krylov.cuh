@@ -297,6 +297,82 @@ __device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t st
   }
 }
 
+// Row product for column c of a multi-vector from the class stencil of a
+// regular row (27 blocks, column indices read from global memory): a real
+// diagonal stencil (kind 2) needs one vector entry and one real multiply-add
+// per block and component; general blocks (kind 1) a full 3x3 product.
+template <typename C, bool kShared>
+__device__ __forceinline__ void row_product_colx_class(const StencilSet* __restrict__ S, int cls, int kind,
+                                                       const int* __restrict__ col, int s0, const C* xs, int xoff,
+                                                       int ldx, int c, C& y0, C& y1, C& y2) {
+  if constexpr (std::is_same<C, float4>::value) {
+    float a[3][4] = {};
+    if (kind == 2) {
+#pragma unroll 3
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xb = 3 * __ldg(col + s0 + kk) * ldx + c - xoff;
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                const float4 xv = kShared ? xs[xb + al * ldx] : ld_cg(xs + xb + al * ldx);
+                const float2 dk = __ldg(&S->dvaldf[cls][al][kk]);
+                df_mac(a[al][0], a[al][1], dk.x, dk.y, xv.x, xv.z);
+                df_mac(a[al][2], a[al][3], dk.x, dk.y, xv.y, xv.w);
+            }
+        }
+    } else {
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xb = 3 * __ldg(col + s0 + kk) * ldx + c - xoff;
+            float4 xv[3];
+#pragma unroll
+            for (int be = 0; be < 3; ++be) xv[be] = kShared ? xs[xb + be * ldx] : ld_cg(xs + xb + be * ldx);
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int be = 0; be < 3; ++be) dfc_mac(a[al], ld_ro(&S->sdf[cls][al][kk][be]), xv[be]);
+        }
+    }
+    y0 = df_result(a[0]);
+    y1 = df_result(a[1]);
+    y2 = df_result(a[2]);
+  } else {
+    using Tr = decltype(C{}.x);
+    constexpr bool kF32 = sizeof(C) == 8;
+    Tr a[6] = {0, 0, 0, 0, 0, 0};
+    if (kind == 2) {
+#pragma unroll 3
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xb = 3 * __ldg(col + s0 + kk) * ldx + c - xoff;
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                const C xv = kShared ? xs[xb + al * ldx] : ld_cg(xs + xb + al * ldx);
+                const Tr dk = kF32 ? (Tr)__ldg(&S->dval32[cls][al][kk]) : (Tr)__ldg(&S->dval[cls][al][kk]);
+                a[2 * al] += dk * xv.x;
+                a[2 * al + 1] += dk * xv.y;
+            }
+        }
+    } else {
+        const C* st = kF32 ? (const C*)S->s32[cls][0][0] : (const C*)S->s64[cls][0][0];
+        for (int kk = 0; kk < 27; ++kk) {
+            const int xb = 3 * __ldg(col + s0 + kk) * ldx + c - xoff;
+            C xv[3];
+#pragma unroll
+            for (int be = 0; be < 3; ++be) xv[be] = kShared ? xs[xb + be * ldx] : ld_cg(xs + xb + be * ldx);
+#pragma unroll
+            for (int al = 0; al < 3; ++al)
+#pragma unroll
+                for (int be = 0; be < 3; ++be) {
+                    const C v = ld_ro(st + (al * 27 + kk) * 3 + be);
+                    a[2 * al] += v.x * xv[be].x - v.y * xv[be].y;
+                    a[2 * al + 1] += v.x * xv[be].y + v.y * xv[be].x;
+                }
+        }
+    }
+    y0 = mk(a[0], a[1]);
+    y1 = mk(a[2], a[3]);
+    y2 = mk(a[4], a[5]);
+  }
+}
+
 // Copies the column indices of the warp's rows [rb, re) into shared memory
 // (one coalesced pass); returns the first block index sb of the range.
 __device__ __forceinline__ int stage_cols(const int* __restrict__ rp, const int* __restrict__ col, int rb, int re,

@@ -296,7 +296,7 @@ extern "C" {
 
 void fe_serve_opts_default(fe_serve_opts* o) {
     if (!o) return;
-    o->precision = FE_PREC_FP64;
+    o->precision = FE_PREC_DF;
     o->tol = 1e-8;
     o->reliable = 1e-4;
     o->max_iter = 20000;

@@ -58,6 +58,7 @@ struct SolveParams {
     const StencilSet* stencil;     // class stencils
     const int* cost_prefix;        // per-row product cost prefix [n_rows + 1] (product phases split by cost)
     int64_t cost_total;            // cost_prefix[n_rows] (host copy, sizes the halo buffer)
+    int cost_min, cost_max;        // bounds of one row's cost (host only: halo sizing)
     const double2* b;
     double2* x;
     double2* r;
@@ -72,9 +73,11 @@ struct SolveParams {
     double* result;
     double tol, reliable;
     int restart;  // 1: a true-residual pass restarts the directions (p = s = 0); 0: keeps them
+    int max_pass;  // iterations after which a restarting pass is replaced anyway (0: no cap)
     int max_iter, max_outer, use_x0;
     int halo;       // bound on |column rank - row rank|
     int stage;      // stage the CTA's uM halo in shared memory (1) or gather from L2 (0)
+    int64_t halo_bytes;  // dynamic shared memory left for the halo (a CTA whose halo is larger gathers)
     int red_bytes;  // dynamic shared memory used by the column sums
     int col_bytes;  // dynamic shared memory for the per-warp column-index staging (R = 1)
     int* rep_status;
@@ -252,10 +255,13 @@ __device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int
 // per-column FP64 partial dots
 //   acc[0..1] = r^T u, acc[2..3] = u^T w, acc[4] = |r|^2,
 //   acc[5..6] = u^T s, acc[7..8] = p^T w, acc[9..10] = p^T s (refresh only).
-template <typename TM, int R, bool kStaged>
+// NV = 5 (no column refreshes) or 11: the refresh accumulators exist only in
+// the NV = 11 instance, which runs after a replacement.
+template <typename TM, int R, bool kStaged, int NV>
 __device__ __forceinline__ bool product_phase(const SolveParams& P, const typename CplxT<TM>::type* xs, int xshift,
                                               int r0, int r1, const int* s_refresh, bool any_refresh, int* s_cols,
-                                              double (&acc)[11]) {
+                                              double (&acc)[NV]) {
+    constexpr bool kRefresh = NV == 11;
     bool ok = true;
     using C = typename CplxT<TM>::type;
     const C* valM = (const C*)P.valM;
@@ -270,22 +276,24 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
         acc[2] += uv.x * wd.x - uv.y * wd.y;
         acc[3] += uv.x * wd.y + uv.y * wd.x;
         acc[4] += rv.x * rv.x + rv.y * rv.y;
-        if (refresh) {
+        if constexpr (kRefresh) {
+          if (refresh) {
             const double2 pv = __ldcg(P.p + o), sd = to_c128(sy);
-            acc[5] += uv.x * sd.x - uv.y * sd.y;
-            acc[6] += uv.x * sd.y + uv.y * sd.x;
-            acc[7] += pv.x * wd.x - pv.y * wd.y;
-            acc[8] += pv.x * wd.y + pv.y * wd.x;
-            acc[9] += pv.x * sd.x - pv.y * sd.y;
-            acc[10] += pv.x * sd.y + pv.y * sd.x;
+            acc[5 % NV] += uv.x * sd.x - uv.y * sd.y;
+            acc[6 % NV] += uv.x * sd.y + uv.y * sd.x;
+            acc[7 % NV] += pv.x * wd.x - pv.y * wd.y;
+            acc[8 % NV] += pv.x * wd.y + pv.y * wd.x;
+            acc[9 % NV] += pv.x * sd.x - pv.y * sd.y;
+            acc[10 % NV] += pv.x * sd.y + pv.y * sd.x;
             P.s[o] = sd;
+          }
         }
     };
     if (R == 1) {
         // one thread per (row, component): ten rows per warp, their column
         // indices staged in shared memory first
         int* cols = s_cols + warp * kColsPerWarp;
-        const bool refresh = s_refresh[0] != 0;
+        const bool refresh = kRefresh && s_refresh[0] != 0;
         const int al = lane % 3;
         for (int rb = r0 + warp * kRowsPerWarpR1; rb < r1; rb += kWarps * kRowsPerWarpR1) {
             const int re = min(rb + kRowsPerWarpR1, r1);
@@ -314,13 +322,24 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
     } else {
         constexpr int kRowsPerWarp = 32 / R;
         const int c = lane % R;
-        const bool refresh = s_refresh[c] != 0;
+        const bool refresh = kRefresh && s_refresh[c] != 0;
         for (int row = r0 + warp * kRowsPerWarp + lane / R; row < r1; row += kWarps * kRowsPerWarp) {
             const int s0 = __ldg(P.rp + row), s1 = __ldg(P.rp + row + 1);
+            const int cls = (kClassPath<C> && P.row_class) ? __ldg(P.row_class + row) : -1;
+            const int kind = cls >= 0 ? __ldg(&P.stencil->kind[cls]) : 0;
             C y[3], sy[3];
-            row_product_colx<C, kStaged>(valM, P.stride, P.col, s0, s1, kStaged ? xs : uM, kStaged ? -xshift : 0, R,
-                                         c, y[0], y[1], y[2]);
-            if (refresh) row_product_colx<C, false>(valM, P.stride, P.col, s0, s1, pM, 0, R, c, sy[0], sy[1], sy[2]);
+            if (kind)
+                row_product_colx_class<C, kStaged>(P.stencil, cls, kind, P.col, s0, kStaged ? xs : uM,
+                                                   kStaged ? -xshift : 0, R, c, y[0], y[1], y[2]);
+            else
+                row_product_colx<C, kStaged>(valM, P.stride, P.col, s0, s1, kStaged ? xs : uM, kStaged ? -xshift : 0,
+                                             R, c, y[0], y[1], y[2]);
+            if (refresh) {
+                if (kind)
+                    row_product_colx_class<C, false>(P.stencil, cls, kind, P.col, s0, pM, 0, R, c, sy[0], sy[1], sy[2]);
+                else
+                    row_product_colx<C, false>(valM, P.stride, P.col, s0, s1, pM, 0, R, c, sy[0], sy[1], sy[2]);
+            }
 #pragma unroll
             for (int al = 0; al < 3; ++al) {
                 const size_t o = (size_t)(3 * row + al) * R + c;
@@ -333,11 +352,39 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
     return ok;
 }
 
+// Diagnostics (FE_TRACE=1): every CTA stamps the end of each phase of its
+// first kTraceIters iterations, [cta][iteration][phase]; after those stamps
+// come kTraceStats values per CTA describing its product rows.
+constexpr int kTraceStats = 8;
 #define FE_TRACE_MARK(k)                                                                        \
     do {                                                                                        \
-        if (P.trace && tid == 0 && trace_it < kTraceIters && cta == P.n_cta / 2)       \
-            P.trace[((size_t)trace_it) * kTracePhases + (k)] = globaltimer_ns();                 \
+        if (P.trace && tid == 0 && trace_it < kTraceIters)                                      \
+            P.trace[((size_t)cta * kTraceIters + trace_it) * kTracePhases + (k)] = globaltimer_ns(); \
     } while (0)
+
+// Product phase of one CTA: optional TMA staging of its halo of uM, then the
+// products with NV fused dots.  Returns false when a bounded wait expired (the
+// error is recorded).
+template <typename TM, int R, int NV>
+__device__ __forceinline__ bool product_step(const SolveParams& P, int cta, bool stage_fits,
+                                             const typename CplxT<TM>::type* uM, int pr0, int pr1, char* halo_buf,
+                                             uint64_t* mbar, unsigned& mbar_phase, const int* s_refresh,
+                                             bool any_refresh, int* s_cols, double (&acc)[NV], int trace_it) {
+    using C = typename CplxT<TM>::type;
+    const int tid = threadIdx.x;
+    bool ok;
+    if (stage_fits) {
+        int shift = 0;
+        if (!stage_halo<C, R>(P, uM, pr0, pr1, halo_buf, mbar, mbar_phase, shift)) return false;
+        FE_TRACE_MARK(1);
+        ok = product_phase<TM, R, true, NV>(P, (const C*)halo_buf, shift, pr0, pr1, s_refresh, any_refresh, s_cols,
+                                            acc);
+    } else {
+        ok = product_phase<TM, R, false, NV>(P, nullptr, 0, pr0, pr1, s_refresh, any_refresh, s_cols, acc);
+    }
+    if (!ok && tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
+    return ok;
+}
 
 // The persistent solve of A X = B for R right-hand sides.
 //   [R] replacement: r = b - A x in FP64 for the columns that ask for it
@@ -368,7 +415,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     __shared__ double s_bn[R], s_rr_ref[R], s_rel[R];
     __shared__ double s_gam_r[R], s_gam_i[R], s_al_r[R], s_al_i[R], s_be_r[R], s_be_i[R];
     __shared__ int s_active[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_first[R], s_refresh[R],
-        s_repl[R];
+        s_repl[R], s_pass_it[R];
     __shared__ int s_any_repl, s_any_active, s_any_refresh;
     __shared__ double2 s_exch[kThreads];
 
@@ -391,6 +438,33 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     }
     __syncthreads();
     const int pr0 = s_pr[0], pr1 = s_pr[1];
+    if (P.trace && tid == 0) {  // product rows of this CTA: explicit rows and blocks, general, diagonal
+        unsigned long long ne = 0, nb = 0, ng = 0, nd = 0;
+        for (int row = pr0; row < pr1; ++row) {
+            const int c = (kClassPath<TM> && P.row_class) ? P.row_class[row] : -1;
+            const int kind = c >= 0 ? P.stencil->kind[c] : 0;
+            if (kind == 1) ++ng;
+            else if (kind == 2) ++nd;
+            else {
+                ++ne;
+                nb += (unsigned long long)(P.rp[row + 1] - P.rp[row]);
+            }
+        }
+        unsigned long long* st = P.trace + (size_t)P.n_cta * kTraceIters * kTracePhases + (size_t)cta * kTraceStats;
+        st[0] = (unsigned long long)pr0;
+        st[1] = (unsigned long long)pr1;
+        st[2] = ne;
+        st[3] = nb;
+        st[4] = ng;
+        st[5] = nd;
+    }
+    // stage the product input only if this CTA's halo fits the buffer
+    const bool stage_fits = P.stage && [&] {
+        const int h0 = max(0, pr0 - P.halo), h1 = min(P.n_rows, pr1 + P.halo);
+        const size_t a0 = ((size_t)3 * h0 * R * sizeof(C)) & ~(size_t)15;
+        const size_t a1 = ((size_t)3 * h1 * R * sizeof(C) + 15) & ~(size_t)15;
+        return a1 - a0 <= (size_t)P.halo_bytes;
+    }();
     const int n_items = (r1 - r0) * R;  // (node, column) pairs owned by this CTA
     const int my_c = tid % R;           // column of every item this thread handles
     const size_t base_o = (size_t)3 * r0 * R;
@@ -402,6 +476,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         s_done[tid] = 0;
         s_status[tid] = FE_OK;
         s_iters[tid] = 0;
+        s_pass_it[tid] = 0;
         s_outer[tid] = 0;
         s_active[tid] = 0;
         s_first[tid] = 1;
@@ -497,6 +572,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     } else {
                         s_active[c] = 1;
                         s_rr_ref[c] = rn * rn;
+                        s_pass_it[c] = 0;
                         s_refresh[c] = s_first[c] ? 0 : 1;
                     }
                 } else if (s_repl[c]) {
@@ -554,35 +630,26 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
 
         // ---- [A] products and fused dots ----
         FE_TRACE_MARK(0);
-        {
+        if (s_any_refresh) {
             double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-            if (P.stage) {
-                int shift = 0;
-                if (!stage_halo<C, R>(P, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, shift)) goto out;
-                FE_TRACE_MARK(1);
-                if (!product_phase<TM, R, true>(P, (const C*)halo_buf, shift, pr0, pr1, s_refresh, s_any_refresh, s_cols,
-                                                acc)) {
-                    if (tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
-                    goto out;
-                }
-            } else {
-                if (!product_phase<TM, R, false>(P, nullptr, 0, pr0, pr1, s_refresh, s_any_refresh, s_cols, acc)) {
-                    if (tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
-                    goto out;
-                }
-            }
+            if (!product_step<TM, R, 11>(P, cta, stage_fits, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, s_refresh,
+                                         s_any_refresh, s_cols, acc, trace_it))
+                goto out;
             FE_TRACE_MARK(2);
-            if (s_any_refresh) {
-                cta_colsum<R, 11>(acc, s_red, s_in);
-                if (!grid_reduce<11 * R>(P, cta, s_in, s_out)) goto out;
-            } else {
-                double a5[5] = {acc[0], acc[1], acc[2], acc[3], acc[4]};
-                cta_colsum<R, 5>(a5, s_red, s_in);
-                FE_TRACE_MARK(3);
-                if (!grid_reduce<5 * R>(P, cta, s_in, s_out)) goto out;
-            }
-            FE_TRACE_MARK(4);
+            cta_colsum<R, 11>(acc, s_red, s_in);
+            FE_TRACE_MARK(3);
+            if (!grid_reduce<11 * R>(P, cta, s_in, s_out)) goto out;
+        } else {
+            double acc[5] = {0, 0, 0, 0, 0};
+            if (!product_step<TM, R, 5>(P, cta, stage_fits, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, s_refresh,
+                                        s_any_refresh, s_cols, acc, trace_it))
+                goto out;
+            FE_TRACE_MARK(2);
+            cta_colsum<R, 5>(acc, s_red, s_in);
+            FE_TRACE_MARK(3);
+            if (!grid_reduce<5 * R>(P, cta, s_in, s_out)) goto out;
         }
+        FE_TRACE_MARK(4);
         // ---- [B] scalars ----
         // B1: does any column need its true residual first?  (No state of the
         // other columns changes in a replacement round: they redo the same
@@ -593,7 +660,8 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                 const double rr = s_out[4 * R + c];
                 const double tb = P.tol * s_bn[c];
                 const bool small = rr <= tb * tb || rr < P.reliable * P.reliable * s_rr_ref[c];
-                if (!(rr == rr) || s_iters[c] >= P.max_iter || (!s_first[c] && small)) {
+                const bool stalled = P.restart && P.max_pass > 0 && s_pass_it[c] >= P.max_pass;
+                if (!(rr == rr) || s_iters[c] >= P.max_iter || (!s_first[c] && (small || stalled))) {
                     s_repl[c] = 1;
                     if (P.restart) s_first[c] = 1;
                 }
@@ -664,6 +732,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     s_gam_r[c] = gr;
                     s_gam_i[c] = gi;
                     s_iters[c] += 1;
+                    s_pass_it[c] += 1;
                     s_first[c] = 0;
                     s_refresh[c] = 0;
                 }
@@ -840,10 +909,12 @@ static fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
     P.n_cta = std::min(ctx->num_sms, std::max(1, P.n_rows));
     P.red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
     P.col_bytes = R == 1 ? (int)(kWarps * kColsPerWarp * sizeof(int)) : 0;
-    // product phases: a CTA gets at most total cost / n_cta (+1 row) of cost >= 1 per row
-    const int64_t rows_per_cta = std::min<int64_t>(P.n_rows, P.cost_total / P.n_cta + 9);
+    // product phases: a CTA's range costs at most total / n_cta plus one row
+    const int64_t rows_per_cta =
+        std::min<int64_t>(P.n_rows, (P.cost_total / P.n_cta + P.cost_max) / P.cost_min + 2);
     const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
     P.stage = (P.halo > 0 && (size_t)P.red_bytes + P.col_bytes + (size_t)halo_bytes <= kSmemBudget) ? 1 : 0;
+    P.halo_bytes = P.stage ? halo_bytes : 0;
     const size_t dyn = (size_t)P.red_bytes + P.col_bytes + (P.stage ? (size_t)halo_bytes : 0);
     FE_CUDA(cudaFuncSetAttribute((const void*)k_solve<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
@@ -973,6 +1044,8 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.stencil = (const StencilSet*)s->stencil.ptr;
     P.cost_prefix = classes ? (const int*)(df ? s->cost_prefix_alu.ptr : s->cost_prefix.ptr) : nullptr;
     P.cost_total = classes ? (df ? s->cost_total_alu : s->cost_total) : (int64_t)m->n_act;
+    P.cost_min = classes ? s->cost_min[df ? 1 : 0] : 1;
+    P.cost_max = classes ? s->cost_max[df ? 1 : 0] : 1;
     P.b = (const double2*)w.b.ptr;
     P.x = (double2*)w.x.ptr;
     P.r = (double2*)w.r.ptr;
@@ -994,6 +1067,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     // products are accurate enough to keep the directions across refreshes
     P.reliable = prec == FE_PREC_MIXED ? o.reliable : 0.0;
     P.restart = prec == FE_PREC_MIXED ? 1 : 0;
+    P.max_pass = o.max_pass_iter;
     P.max_iter = o.max_iter;
     P.max_outer = o.max_outer;
     P.use_x0 = use_x0 ? 1 : 0;
@@ -1020,7 +1094,8 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
     fe_status e = alloc_workspace(st, n_dof, R, prec, 2 * ctx->num_sms, w);
     if (e != FE_OK) return e;
     const bool tracing = getenv("FE_TRACE") && getenv("FE_TRACE")[0] == '1';
-    const size_t trace_bytes = (size_t)ctx->num_sms * kTraceIters * kTracePhases * sizeof(unsigned long long);
+    const size_t trace_bytes =
+        (size_t)ctx->num_sms * (kTraceIters * kTracePhases + kTraceStats) * sizeof(unsigned long long);
     if (tracing && (e = dev_alloc(st, w.trace, trace_bytes)) != FE_OK) {
         cleanup();
         return e;
@@ -1066,9 +1141,10 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
             cudaMemcpy(tr.data(), w.trace.ptr, trace_bytes, cudaMemcpyDeviceToHost);
             double sum[kTracePhases] = {0};
             int n_it = 0;
+            const size_t mid = (size_t)(P.n_cta / 2) * kTraceIters * kTracePhases;
             for (int it = 1; it + 1 < kTraceIters; ++it) {
-                const unsigned long long* a = &tr[(size_t)it * kTracePhases];
-                const unsigned long long* b = &tr[(size_t)(it + 1) * kTracePhases];
+                const unsigned long long* a = &tr[mid + (size_t)it * kTracePhases];
+                const unsigned long long* b = &tr[mid + (size_t)(it + 1) * kTracePhases];
                 if (!a[0] || !b[0]) break;
                 for (int k = 1; k < kTracePhases; ++k) sum[k] += (double)(a[k] - a[k - 1]);
                 sum[0] += (double)(b[0] - a[kTracePhases - 1]);
@@ -1077,6 +1153,19 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
             fprintf(stderr, "FE_TRACE mid-cta %d iterations, ns per phase:", n_it);
             for (int k = 0; k < kTracePhases; ++k) fprintf(stderr, " %d:%.0f", k, n_it ? sum[k] / n_it : 0.0);
             fprintf(stderr, "\n");
+            // FE_TRACE_DUMP=<path>: raw stamps and per-CTA row counts
+            // (header: n_cta, iterations, phases, stats per CTA, as int64)
+            const char* dump = getenv("FE_TRACE_DUMP");
+            if (dump && dump[0]) {
+                if (FILE* f = fopen(dump, "wb")) {
+                    const long long hdr[4] = {P.n_cta, kTraceIters, kTracePhases, kTraceStats};
+                    fwrite(hdr, sizeof hdr, 1, f);
+                    fwrite(tr.data(), sizeof(unsigned long long), (size_t)P.n_cta * kTraceIters * kTracePhases, f);
+                    fwrite(tr.data() + (size_t)P.n_cta * kTraceIters * kTracePhases, sizeof(unsigned long long),
+                           (size_t)P.n_cta * kTraceStats, f);
+                    fclose(f);
+                }
+            }
         }
         if (hs.err) {
             set_error("solve: a grid barrier wait expired (device status %d)", hs.err);
@@ -1174,7 +1263,8 @@ static fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_
         P.n_cta = n_cta[i];
         P.red_bytes = red_bytes;
         P.col_bytes = col_bytes;
-        const int64_t rows_per_cta = std::min<int64_t>(P.n_rows, P.cost_total / P.n_cta + 9);
+        const int64_t rows_per_cta =
+            std::min<int64_t>(P.n_rows, (P.cost_total / P.n_cta + P.cost_max) / P.cost_min + 2);
         const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
         const size_t need = (size_t)red_bytes + col_bytes + (size_t)halo_bytes;
         P.stage = (P.halo > 0 && need <= kSmemBudget) ? 1 : 0;
@@ -1182,6 +1272,7 @@ static fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_
         cta0[i + 1] = cta0[i] + n_cta[i];
         FE_CUDA(cudaMemsetAsync(P.sync, 0, sizeof(SyncState), ctx->stream));
     }
+    for (int i = 0; i < n; ++i) Ps[i].halo_bytes = (int64_t)dyn - red_bytes - col_bytes;
     const int grid = cta0[n];
     DevBuf dparams, dcta;
     FE_TRY(dev_alloc(ctx->stream, dparams, (size_t)n * sizeof(SolveParams)));
@@ -1343,7 +1434,8 @@ static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
         set_error("solve: precision must be FP64, MIXED or DF");
         return FE_ERR_INVALID_ARG;
     }
-    if (!(out.tol > 0.0) || out.max_iter < 1 || out.max_outer < 1 || !(out.reliable >= 0.0 && out.reliable < 1.0) || out.rhs_tile < 0) {
+    if (!(out.tol > 0.0) || out.max_iter < 1 || out.max_outer < 1 || !(out.reliable >= 0.0 && out.reliable < 1.0) ||
+        out.rhs_tile < 0 || out.max_pass_iter < 0) {
         set_error("solve: bad tolerance or iteration limits");
         return FE_ERR_INVALID_ARG;
     }
@@ -1358,12 +1450,13 @@ extern "C" {
 
 void fe_solve_opts_default(fe_solve_opts* o) {
     if (!o) return;
-    o->precision = FE_PREC_MIXED;
+    o->precision = FE_PREC_DF;
     o->tol = 1e-8;
     o->reliable = 1e-4;
     o->max_iter = 20000;
     o->max_outer = 200;
     o->rhs_tile = 0;
+    o->max_pass_iter = 2000;
 }
 
 fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y) {

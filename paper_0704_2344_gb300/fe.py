@@ -67,7 +67,8 @@ class fe_planewave(C.Structure):
 
 class fe_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
-                ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32)]
+                ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32),
+                ("max_pass_iter", C.c_int32)]
 
 
 class fe_solve_stats(C.Structure):
@@ -282,7 +283,7 @@ def fe_mesh_destroy(mesh):
     load().fe_mesh_destroy(mesh)
 
 
-def fe_assemble(ctx, mesh, freq_hz: float, precision: int = FE_PREC_MIXED):
+def fe_assemble(ctx, mesh, freq_hz: float, precision: int = FE_PREC_DF):
     out = P()
     _check(load().fe_assemble(ctx, mesh, float(freq_hz), int(precision), C.byref(out)), "fe_assemble")
     return out
@@ -350,12 +351,14 @@ def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
     _check(load().fe_spmv(ctx, system, int(precision), int(nrhs), _ptr(x), _ptr(y)), "fe_spmv")
 
 
-def solve_opts(precision=FE_PREC_MIXED, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
-               rhs_tile=0) -> fe_solve_opts:
+def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
+               rhs_tile=0, max_pass_iter=None) -> fe_solve_opts:
     o = fe_solve_opts()
     load().fe_solve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
     o.max_iter, o.max_outer, o.rhs_tile = int(max_iter), int(max_outer), int(rhs_tile)
+    if max_pass_iter is not None:
+        o.max_pass_iter = int(max_pass_iter)
     return o
 
 
@@ -413,7 +416,7 @@ def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_op
 
 # --------------------------------------------------------------------------
 # Serving
-def serve_opts(precision=FE_PREC_FP64, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
+def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
                hbm_budget=0, max_ctas=0, work_per_cta=0) -> fe_serve_opts:
     o = fe_serve_opts()
     load().fe_serve_opts_default(C.byref(o))

@@ -35,9 +35,13 @@ def test_nm_exports(fe):
 
 
 def test_option_defaults_without_gpu(fe):
-    o = fe.solve_opts()
-    assert o.precision == fe.FE_PREC_MIXED and o.tol == 1e-8 and o.max_iter == 20000
     import ctypes
+    o = fe.fe_solve_opts()
+    fe.load().fe_solve_opts_default(ctypes.byref(o))
+    assert o.precision == fe.FE_PREC_DF and o.tol == 1e-8 and o.max_iter == 20000 and o.max_pass_iter == 2000
+    s = fe.fe_serve_opts()
+    fe.load().fe_serve_opts_default(ctypes.byref(s))
+    assert s.precision == fe.FE_PREC_DF and s.tol == 1e-8 and s.work_per_cta == 2048
     opt = fe.fe_options()
     fe.load().fe_options_default(ctypes.byref(opt))
     assert opt.variant == fe.FE_VARIANT_S and opt.abc_sigma == 1.0 and opt.penalty_s == 1.0

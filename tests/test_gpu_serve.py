@@ -117,8 +117,8 @@ def test_serve_memory_budget(fe, ctx):
     budget; a request larger than the whole budget fails with FE_ERR_OOM."""
     rng = np.random.default_rng(21)
     reqs = [(W.pec_box_problem(8, 3e9, rng, name=f"b{i}"), W.random_waves(2, rng)) for i in range(4)]
-    budget = 8 << 20  # each request's estimate is about 5 MiB
-    srv = fe.fe_serve_create(ctx, fe.serve_opts(hbm_budget=budget))
+    budget = 12 << 20  # each request's estimate is about 8.2 MiB in the FP32-pair mode
+    srv = fe.fe_serve_create(ctx, fe.serve_opts(precision=fe.FE_PREC_DF, hbm_budget=budget))
     try:
         tickets = [fe.fe_serve_submit(srv, p, w) for p, w in reqs]
         big = W.empty_box(60, name="big")

@@ -66,11 +66,11 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(fe, ctx):
         x = torch.zeros_like(b)
         torch.cuda.synchronize()
         with pytest.raises(fe.FeError) as err:
-            fe.fe_solve_rhs_noalloc(ctx, system, 8, b, x)
+            fe.fe_solve_rhs_noalloc(ctx, system, 8, b, x, fe.solve_opts(precision=fe.FE_PREC_MIXED))
         assert err.value.status == fe.FE_ERR_INVALID_ARG
         assert "scratch" in str(err.value)
         with pytest.raises(fe.FeError) as err:
-            fe.fe_solve_rhs_noalloc(ctx, system, 3, b, x)  # not a supported width
+            fe.fe_solve_rhs_noalloc(ctx, system, 3, b, x, fe.solve_opts(precision=fe.FE_PREC_MIXED))  # not a width
         assert err.value.status == fe.FE_ERR_INVALID_ARG
     finally:
         fe.fe_system_destroy(system)
