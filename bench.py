@@ -46,8 +46,8 @@ def parse():
                     help="auto: time both and report the faster one that reaches the tolerance")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
-    ap.add_argument("--requests", type=int, default=128,
-                    help="config5: requests in the serving stream (the full stream has 512)")
+    ap.add_argument("--requests", type=int, default=32,
+                    help="config5: requests in the serving stream, its first ones (the full stream has 512)")
     ap.add_argument("--serve-precision", default="df", choices=["df", "fp64", "mixed"])
     return ap.parse_args()
 
@@ -445,10 +445,24 @@ def run_serving(args, rank, world, local_rank):
         seq_ok += bool(sequential(q))
         seq_times.append(time.perf_counter() - ts)
     seq_wall = time.perf_counter() - t0
+    print(f"config5: sequential FP64 {len(reqs)} requests in {seq_wall:.1f} s ({seq_ok} converged)", file=sys.stderr,
+          flush=True)
 
     with ClockSampler(local_rank) as clocks:
         wall, res, info = serve([0.0] * len(reqs))
     ok = sum(r["status"] == fe.FE_OK for r in res)
+
+    def describe(i, r):
+        its = [rep["iterations"] for rep in (r["reports"] or [])]
+        rel = [rep["rel_residual"] for rep in (r["reports"] or [])]
+        return {"request": i, "nodes_per_side": int(reqs[i].problem.nx + 1), "n_dof": r["n_dof"], "nrhs": r["nrhs"],
+                "status": r["status"], "max_iterations": max(its) if its else None,
+                "max_rel_residual": max(rel) if rel else None, "service_s": round(r["t_done"] - r["t_admit"], 3),
+                "batch_jobs": r["batch_jobs"], "batch_ctas": r["batch_ctas"], "message": r["message"][:120]}
+    slowest = sorted(range(len(res)), key=lambda i: res[i]["t_done"] - res[i]["t_admit"])[-5:]
+    failed = [describe(i, r) for i, r in enumerate(res) if r["status"] != fe.FE_OK]
+    print(f"config5: served all at t=0 in {wall:.1f} s ({ok} converged, {info['launches']} launches)",
+          file=sys.stderr, flush=True)
 
     rng = np.random.default_rng(20070704 + 55 + rank)
     gaps = rng.exponential(1.25 * float(np.mean(seq_times)), len(reqs))
@@ -473,6 +487,7 @@ def run_serving(args, rank, world, local_rank):
                    "serve_precision": args.serve_precision, "tol": 1e-8,
                    "l2": "inputs of successive requests differ; no flush", "parallelism": f"replicas x{world}"},
         "served_ok": ok, "sequential_ok": seq_ok,
+        "served_failed": failed, "served_slowest": [describe(i, res[i]) for i in reversed(slowest)],
         "sequential_fp64": {"value": round(total_solves / seq_wall, 3), "unit": "solves/s",
                             "wall_s": round(seq_wall, 3),
                             "p50_s": round(float(np.percentile(seq_lat, 50)), 5),

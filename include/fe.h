@@ -229,7 +229,7 @@ typedef struct fe_solve_opts {
     double reliable;     /* mixed mode: each time the recursive residual has dropped by this factor since the
                             last FP64 pass, the FP64 true residual b - A x replaces it and the complex64
                             Krylov directions restart (iterative refinement); default 1e-4 */
-    int32_t max_iter;    /* cap on Krylov iterations per right-hand side; default 20000 */
+    int32_t max_iter;    /* cap on Krylov iterations per right-hand side; default 100000 */
     int32_t max_outer;   /* cap on true-residual replacements per right-hand side; default 200 */
     int32_t rhs_tile;    /* right-hand sides per device pass, 0 = automatic */
     int32_t max_pass_iter; /* mixed mode: a complex64 pass that has not dropped by `reliable` after this
@@ -308,11 +308,13 @@ typedef struct fe_serve_opts {
     int32_t precision;     /* FE_PREC_DF (default), FE_PREC_FP64 or FE_PREC_MIXED, for every request */
     double tol;            /* true relative residual target; default 1e-8 */
     double reliable;       /* FE_PREC_MIXED refinement trigger; default 1e-4 */
-    int32_t max_iter;      /* default 20000 */
+    int32_t max_iter;      /* default 100000 */
     int32_t max_outer;     /* default 200 */
     int64_t hbm_budget;    /* device bytes for admitted requests; 0: 80 % of the free memory at creation */
     int32_t max_ctas;      /* CTAs of one launch, 1..one per SM; 0: one per SM */
     int32_t work_per_cta;  /* packing target, block rows x tile width per CTA; 0: 2048 */
+    int32_t max_job_ctas;  /* CTAs one request may take, so that a large request leaves room for others;
+                              0: half the SMs */
 } fe_serve_opts;
 void fe_serve_opts_default(fe_serve_opts* o);
 
@@ -372,11 +374,12 @@ void fe_serve_destroy(fe_server* srv);
  * fills n_cta[i] (0: not in this launch) for one launch of at most max_ctas
  * CTAs and returns how many requests it takes.  The oldest request is always
  * taken; others of its width follow in order while their CTA demand,
- * ceil(rows x width / work_per_cta) clamped to 1..rows, fits; CTAs left over
- * go one at a time to the taken request with the most work per CTA while it
- * keeps at least work_per_cta / 4 per CTA. */
-int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t work_per_cta,
-                      int32_t* n_cta);
+ * ceil(rows x width / work_per_cta) clamped to 1..min(rows, max_job_ctas),
+ * fits; CTAs left over go one at a time to the taken request with the most
+ * work per CTA while it keeps at least work_per_cta / 4 per CTA and stays
+ * within max_job_ctas (values < 1 or > max_ctas mean max_ctas). */
+int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,
+                      int32_t work_per_cta, int32_t* n_cta);
 
 /* Device-side statistics of the most recent fe_solve_batch / fe_solve_rhs
  * call on this context, measured with CUDA events on the context stream

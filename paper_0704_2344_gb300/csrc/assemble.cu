@@ -147,7 +147,8 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                                                   const double2* __restrict__ tab, double2* __restrict__ val64,
                                                   float2* __restrict__ val32, float4* __restrict__ valdf,
                                                   double2* __restrict__ dinv64, float2* __restrict__ dinv32,
-                                                  int n_act, int64_t stride, int* __restrict__ status) {
+                                                  float4* __restrict__ dinvdf, int n_act, int64_t stride,
+                                                  int* __restrict__ status) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_act) return;
@@ -259,6 +260,7 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                 if (dinv32)
                     dinv32[(size_t)warp * 9 + 3 * r + c] =
                         make_float2(__double2float_rn(v.re), __double2float_rn(v.im));
+                if (dinvdf) dinvdf[(size_t)warp * 9 + 3 * r + c] = df_pair(make_double2(v.re, v.im));
             }
     }
 }
@@ -383,8 +385,8 @@ __global__ void k_row_cost(const signed char* __restrict__ cls, const StencilSet
 
 static void system_free(fe_system* s) {
     cudaStream_t st = s->ctx->stream;
-    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->row_class,
-                      &s->stencil, &s->cost_prefix, &s->cost_prefix_alu})
+    for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
+                      &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu})
         dev_free(st, *b);
 }
 
@@ -440,6 +442,7 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
     }
     if (precision == FE_PREC_DF) {
         if ((e = dev_alloc(st, s->valdf, (size_t)s->stride * 9 * sizeof(float4))) != FE_OK) return fail(e);
+        if ((e = dev_alloc(st, s->dinvdf, (size_t)m->n_act * 9 * sizeof(float4))) != FE_OK) return fail(e);
     }
     TableParams P{};
     for (int a = 0; a < 3; ++a) P.h[a] = m->h[a];
@@ -469,7 +472,8 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
                                            (const int*)m->node_id.ptr, (const int*)m->row_ptr.ptr,
                                            (const double2*)s->tables.ptr, (double2*)s->val64.ptr,
                                            (float2*)s->val32.ptr, (float4*)s->valdf.ptr, (double2*)s->dinv64.ptr,
-                                           (float2*)s->dinv32.ptr, m->n_act, s->stride, d_status);
+                                           (float2*)s->dinv32.ptr, (float4*)s->dinvdf.ptr, m->n_act, s->stride,
+                                           d_status);
     {
         count_launches(1);
         cudaError_t ce = cudaGetLastError();
@@ -552,8 +556,8 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
     out->rows_diagonal = s->rows_diagonal;
     out->blocks_explicit = s->blocks_explicit;
     int64_t bytes = 0;
-    for (const DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->row_class,
-                            &s->stencil, &s->cost_prefix, &s->cost_prefix_alu})
+    for (const DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
+                            &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu})
         bytes += (int64_t)b->bytes;
     out->device_bytes = bytes;
     return FE_OK;

@@ -102,6 +102,7 @@ struct fe_system {
     fe::DevBuf val64, val32;         // double2 / float2 [9 * stride]
     fe::DevBuf valdf;                // float4 [9 * stride]: FP32 pairs (re_hi, im_hi, re_lo, im_lo), FE_PREC_DF
     fe::DevBuf dinv64, dinv32;       // double2 / float2 [n_act * 9]
+    fe::DevBuf dinvdf;               // float4 [n_act * 9]: FP32 pairs of dinv64, FE_PREC_DF
     // Regular rows: interior nodes whose 8 elements are active, of one
     // material and have no outer or PEC face.  All regular rows of a material
     // carry the same 27 blocks (same element tables, same summation order), so

@@ -61,6 +61,36 @@ __device__ __forceinline__ void dfc_mac(float (&acc)[4], const float4& m, const 
 
 __device__ __forceinline__ float4 df_result(const float (&acc)[4]) { return make_float4(acc[0], acc[2], acc[1], acc[3]); }
 
+// acc (4 floats as above) += m * x through a pointer.
+__device__ __forceinline__ void dfc_mac4(float* acc, const float4& m, const float4& x) {
+    df_mac(acc[0], acc[1], m.x, m.z, x.x, x.z);
+    df_mac(acc[0], acc[1], -m.y, -m.w, x.y, x.w);
+    df_mac(acc[2], acc[3], m.x, m.z, x.y, x.w);
+    df_mac(acc[2], acc[3], m.y, m.w, x.x, x.z);
+}
+
+// Canonical pair of h + l (TwoSum: h = RN(h + l), l = the exact remainder).
+__device__ __forceinline__ void df_norm(float& h, float& l) {
+    const float t = __fadd_rn(h, l);
+    const float v = __fsub_rn(t, h);
+    l = __fadd_rn(__fsub_rn(h, __fsub_rn(t, v)), __fsub_rn(l, v));
+    h = t;
+}
+
+// Accumulator -> stored complex FP32 pair, renormalised.
+__device__ __forceinline__ float4 df_result_norm(float (&acc)[4]) {
+    df_norm(acc[0], acc[1]);
+    df_norm(acc[2], acc[3]);
+    return make_float4(acc[0], acc[2], acc[1], acc[3]);
+}
+
+// y + a * x for complex FP32 pairs.
+__device__ __forceinline__ float4 dfc_axpy(const float4& y, const float4& a, const float4& x) {
+    float acc[4] = {y.x, y.z, y.y, y.w};
+    dfc_mac(acc, a, x);
+    return df_result_norm(acc);
+}
+
 __device__ __forceinline__ float2 mk(float r, float i) { return make_float2(r, i); }
 __device__ __forceinline__ double2 mk(double r, double i) { return make_double2(r, i); }
 

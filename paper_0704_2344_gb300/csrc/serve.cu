@@ -205,7 +205,8 @@ bool worker_turn(fe_server* S) {
         width[i] = job_width(S->ready[i]->job);
     }
     const int max_ctas = S->o.max_ctas > 0 ? std::min(S->o.max_ctas, S->ictx->num_sms) : S->ictx->num_sms;
-    fe_serve_plan(n, rows.data(), width.data(), max_ctas, S->o.work_per_cta, n_cta.data());
+    const int max_job = S->o.max_job_ctas > 0 ? std::min(S->o.max_job_ctas, max_ctas) : std::max(1, max_ctas / 2);
+    fe_serve_plan(n, rows.data(), width.data(), max_ctas, max_job, S->o.work_per_cta, n_cta.data());
     std::vector<ServeReq*> batch, rest;
     std::vector<SolveJob*> jobs;
     std::vector<int> ctas;
@@ -299,17 +300,19 @@ void fe_serve_opts_default(fe_serve_opts* o) {
     o->precision = FE_PREC_DF;
     o->tol = 1e-8;
     o->reliable = 1e-4;
-    o->max_iter = 20000;
+    o->max_iter = 100000;
     o->max_outer = 200;
     o->hbm_budget = 0;
     o->max_ctas = 0;
     o->work_per_cta = 2048;
+    o->max_job_ctas = 0;
 }
 
-int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t work_per_cta,
-                      int32_t* n_cta) {
+int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,
+                      int32_t work_per_cta, int32_t* n_cta) {
     if (n <= 0 || !rows || !width || !n_cta || max_ctas < 1) return 0;
     if (work_per_cta < 1) work_per_cta = 2048;
+    if (max_job_ctas < 1 || max_job_ctas > max_ctas) max_job_ctas = max_ctas;
     for (int i = 0; i < n; ++i) n_cta[i] = 0;
     const int32_t W = width[0];
     int32_t remaining = max_ctas, taken = 0;
@@ -317,7 +320,7 @@ int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int3
         if (width[i] != W) continue;
         const int64_t r = std::max<int64_t>(rows[i], 1);
         int64_t want = (r * width[i] + work_per_cta - 1) / work_per_cta;
-        want = std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(r, max_ctas)));
+        want = std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(r, max_job_ctas)));
         if (want > remaining) {
             if (i != 0) continue;  // a later, smaller request may still fit
             want = remaining;
@@ -332,7 +335,7 @@ int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int3
         int best = -1;
         double best_w = 0.0;
         for (int i = 0; i < n; ++i) {
-            if (n_cta[i] == 0 || n_cta[i] >= std::max<int64_t>(rows[i], 1)) continue;
+            if (n_cta[i] == 0 || n_cta[i] >= std::min<int64_t>(std::max<int64_t>(rows[i], 1), max_job_ctas)) continue;
             const double w = (double)std::max<int64_t>(rows[i], 1) * width[i] / (n_cta[i] + 1);
             if (w >= 0.25 * work_per_cta && w > best_w) {
                 best_w = w;
@@ -358,7 +361,8 @@ fe_status fe_serve_create(fe_ctx* ctx, const fe_serve_opts* opt, fe_server** out
     if (o.work_per_cta <= 0) o.work_per_cta = 2048;
     if ((o.precision != FE_PREC_FP64 && o.precision != FE_PREC_MIXED && o.precision != FE_PREC_DF) ||
         !(o.tol > 0.0) || o.max_iter < 1 ||
-        o.max_outer < 1 || !(o.reliable >= 0.0 && o.reliable < 1.0) || o.hbm_budget < 0 || o.max_ctas < 0) {
+        o.max_outer < 1 || !(o.reliable >= 0.0 && o.reliable < 1.0) || o.hbm_budget < 0 || o.max_ctas < 0 ||
+        o.max_job_ctas < 0) {
         set_error("fe_serve_create: option out of range");
         return FE_ERR_INVALID_ARG;
     }

@@ -54,6 +54,7 @@ struct SolveParams {
     const void* valM;       // matrix in the inner precision
     int64_t stride;         // plane stride of the block values
     const double2* dinv64;  // block-Jacobi inverse, applied in FP64
+    const float4* dinvdf;   // its FP32 pairs (FE_PREC_DF: Krylov vectors are FP32 pairs)
     const signed char* row_class;  // regular-row class per row (-1: explicit blocks)
     const StencilSet* stencil;     // class stencils
     const int* cost_prefix;        // per-row product cost prefix [n_rows + 1] (product phases split by cost)
@@ -262,6 +263,10 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
                                               int r0, int r1, const int* s_refresh, bool any_refresh, int* s_cols,
                                               double (&acc)[NV]) {
     constexpr bool kRefresh = NV == 11;
+    // FP32-pair vectors: dots accumulate as FP32 pairs, facc[2k] + facc[2k+1]
+    // is acc[k] (converted to FP64 once, at the end of the phase)
+    constexpr bool kDFV = std::is_same<TM, DFloat>::value && (R > 1);
+    float facc[kDFV ? 2 * NV : 1] = {};
     bool ok = true;
     using C = typename CplxT<TM>::type;
     const C* valM = (const C*)P.valM;
@@ -270,6 +275,22 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
     C* w = (C*)P.w;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     auto dots = [&](size_t o, const C& wy, bool refresh, const C& sy) {
+      if constexpr (kDFV) {
+        const float4 rv = ld_cg((const float4*)P.r + o), uv = ld_cg((const float4*)P.u + o);
+        dfc_mac4(facc + 0, rv, uv);
+        dfc_mac4(facc + 4, uv, wy);
+        df_mac(facc[8], facc[9], rv.x, rv.z, rv.x, rv.z);
+        df_mac(facc[8], facc[9], rv.y, rv.w, rv.y, rv.w);
+        if constexpr (kRefresh) {
+          if (refresh) {
+            const float4 pv = ld_cg((const float4*)P.p + o);
+            dfc_mac4(facc + 10 % (2 * NV), uv, sy);
+            dfc_mac4(facc + 14 % (2 * NV), pv, wy);
+            dfc_mac4(facc + 18 % (2 * NV), pv, sy);
+            ((float4*)P.s)[o] = sy;
+          }
+        }
+      } else {
         const double2 rv = __ldcg(P.r + o), uv = __ldcg(P.u + o), wd = to_c128(wy);
         acc[0] += rv.x * uv.x - rv.y * uv.y;
         acc[1] += rv.x * uv.y + rv.y * uv.x;
@@ -288,6 +309,7 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             P.s[o] = sd;
           }
         }
+      }
     };
     if (R == 1) {
         // one thread per (row, component): ten rows per warp, their column
@@ -348,6 +370,10 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             }
         }
     }
+    if constexpr (kDFV) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) acc[k] += (double)facc[2 * k] + (double)facc[2 * k + 1];
+    }
     (void)any_refresh;
     return ok;
 }
@@ -401,10 +427,21 @@ __device__ __forceinline__ bool product_step(const SolveParams& P, int cta, bool
 template <typename TM, int R>
 __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) {
     using C = typename CplxT<TM>::type;
+    // Krylov vectors: FP64, or FP32 pairs in the FE_PREC_DF mode with several
+    // columns (then the products read u and p directly and the updates run
+    // on the FP32 pipes; with one column the FP64 recurrences converge in
+    // fewer iterations and the update is cheap either way)
+    constexpr bool kDFV = std::is_same<TM, DFloat>::value && (R > 1);
+    using VT = std::conditional_t<kDFV, float4, double2>;
+    VT* X = (VT*)P.x;
+    VT* Rv = (VT*)P.r;
+    VT* U = (VT*)P.u;
+    VT* Pv = (VT*)P.p;
+    VT* Sv = (VT*)P.s;
     C* uM = (C*)P.uM;
     C* pM = (C*)P.pM;
     const C* wv = (const C*)P.w;
-    constexpr bool kSplit = !std::is_same<C, double2>::value;  // inner copies are separate buffers
+    constexpr bool kSplit = !std::is_same<C, VT>::value;  // inner copies are separate buffers
 
     extern __shared__ __align__(128) char dyn[];
     double* s_red = (double*)dyn;
@@ -486,7 +523,8 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         s_bn[tid] = 0.0;
     }
     for (int i = tid; i < 3 * n_items; i += kThreads) {
-        if (!P.use_x0) P.x[base_o + i] = make_double2(0.0, 0.0);
+        if (!P.use_x0) P.x[base_o + i] = make_double2(0.0, 0.0);  // zero bits: also a zero FP32 pair
+        else if constexpr (kDFV) X[base_o + i] = from_c128<float4>(P.x[base_o + i]);  // in place, same size
         P.p[base_o + i] = make_double2(0.0, 0.0);
         P.s[base_o + i] = make_double2(0.0, 0.0);
     }
@@ -497,7 +535,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     for (;;) {
         if (s_any_repl) {
             // ---- [R] FP64 true residual for the columns that ask for it ----
+            if constexpr (kDFV) {  // FP64 copy of x for the product (w is free until the next product)
+                double2* xd = (double2*)P.w;
+                for (int i = tid; i < 3 * n_items; i += kThreads) xd[base_o + i] = to_c128(X[base_o + i]);
+                if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
+            }
             {
+                const double2* xsrc = kDFV ? (const double2*)P.w : P.x;
                 double acc[2] = {0.0, 0.0};
                 const int lane = tid & 31, warp = tid >> 5;
                 if (R == 1) {
@@ -516,11 +560,11 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                                 const int kind = cls >= 0 ? __ldg(&P.stencil->kind[cls]) : 0;
                                 const double2 y =
                                     kind ? row_component_class<double2, false>(P.stencil, cls, kind, cols + (s0 - sb),
-                                                                               al, P.x, 0)
+                                                                               al, xsrc, 0)
                                          : row_component<double2, false>(P.val64, P.stride, cols + (s0 - sb), s0, s1,
-                                                                         al, P.x, 0);
+                                                                         al, xsrc, 0);
                                 const double2 rv = make_double2(bv.x - y.x, bv.y - y.y);
-                                P.r[o] = rv;
+                                Rv[o] = from_c128<VT>(rv);
                                 acc[0] += rv.x * rv.x + rv.y * rv.y;
                                 acc[1] += bv.x * bv.x + bv.y * bv.y;
                             }
@@ -535,13 +579,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                              row += kWarps * kRowsPerWarp) {
                             double2 y[3];
                             row_product_colx<double2, false>(P.val64, P.stride, P.col, __ldg(P.rp + row),
-                                                             __ldg(P.rp + row + 1), P.x, 0, R, c, y[0], y[1], y[2]);
+                                                             __ldg(P.rp + row + 1), xsrc, 0, R, c, y[0], y[1], y[2]);
 #pragma unroll
                             for (int al = 0; al < 3; ++al) {
                                 const size_t o = (size_t)(3 * row + al) * R + c;
                                 const double2 bv = __ldg(P.b + o);
                                 const double2 rv = make_double2(bv.x - y[al].x, bv.y - y[al].y);
-                                P.r[o] = rv;
+                                Rv[o] = from_c128<VT>(rv);
                                 acc[0] += rv.x * rv.x + rv.y * rv.y;
                                 acc[1] += bv.x * bv.x + bv.y * bv.y;
                             }
@@ -591,7 +635,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     const size_t o = base_o + i;
                     double2 rv = make_double2(0.0, 0.0);
                     if (valid) {
-                        rv = __ldcg(P.r + o);
+                        rv = to_c128(ld_cg(Rv + o));
                         if (kSplit) pM[o] = from_c128<C>(__ldcg(P.p + o));
                     }
                     s_exch[tid] = rv;
@@ -603,7 +647,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                         double2 uu = make_double2(0.0, 0.0);
 #pragma unroll
                         for (int be = 0; be < 3; ++be) uu = cfma(__ldg(drow + be), s_exch[tid + (be - al) * R], uu);
-                        P.u[o] = uu;
+                        U[o] = from_c128<VT>(uu);
                         if (kSplit) uM[o] = from_c128<C>(uu);
                     }
                     __syncthreads();
@@ -763,6 +807,38 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             const double2 beta = make_double2(s_be_r[my_c], s_be_i[my_c]);
             constexpr int kChunk = (kThreads / (3 * R)) * (3 * R);
             const int n3 = 3 * n_items;
+            if constexpr (kDFV) {  // the same update in FP32-pair arithmetic
+                const float4 a4 = from_c128<float4>(alpha), na4 = from_c128<float4>(nalpha);
+                const float4 b4 = from_c128<float4>(beta);
+                float4* ex = (float4*)s_exch;
+                for (int base = 0; base < n3; base += kChunk) {
+                    const int i = base + tid;
+                    const bool valid = act && tid < kChunk && i < n3;
+                    const size_t o = base_o + i;
+                    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (valid) {
+                        const float4 pp = dfc_axpy(ld_cg(U + o), b4, ld_cg(Pv + o));
+                        const float4 ss = dfc_axpy(ld_cg(wv + o), b4, ld_cg(Sv + o));
+                        Pv[o] = pp;
+                        Sv[o] = ss;
+                        X[o] = dfc_axpy(ld_cg(X + o), a4, pp);
+                        rn = dfc_axpy(ld_cg(Rv + o), na4, ss);
+                        Rv[o] = rn;
+                    }
+                    ex[tid] = rn;
+                    __syncthreads();
+                    if (valid) {
+                        const int node = r0 + i / (3 * R);
+                        const int al = (i / R) % 3;
+                        const float4* drow = P.dinvdf + (size_t)node * 9 + 3 * al;
+                        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) dfc_mac(acc, __ldg(drow + be), ex[tid + (be - al) * R]);
+                        U[o] = df_result_norm(acc);
+                    }
+                    __syncthreads();
+                }
+            } else
             for (int base = 0; base < n3; base += kChunk) {
                 const int i = base + tid;
                 const bool valid = act && tid < kChunk && i < n3;
@@ -798,6 +874,10 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         ++trace_it;
     }
 out:
+    if constexpr (kDFV) {  // the solution back to FP64, in place (every CTA its own rows)
+        __syncthreads();
+        for (int i = tid; i < 3 * n_items; i += kThreads) P.x[base_o + i] = to_c128(X[base_o + i]);
+    }
     if (cta == 0 && tid < R) {
         P.rep_status[tid] = s_status[tid];
         P.rep_iters[tid] = s_iters[tid];
@@ -966,6 +1046,10 @@ static void free_workspace(cudaStream_t st, Workspace& w) {
 // complex64 or a complex FP32 pair.
 static size_t inner_bytes(int prec) { return prec == FE_PREC_MIXED ? sizeof(float2) : sizeof(double2); }
 
+// Whether the products read separate inner-precision copies of u and p
+// (complex64; FP32 pairs with one column) instead of the vectors themselves.
+static bool split_copies(int prec, int R) { return prec == FE_PREC_MIXED || (prec == FE_PREC_DF && R == 1); }
+
 // Inner-precision matrix planes of a system, or NULL when it was not
 // assembled for that precision.
 static const void* inner_matrix(const fe_system* s, int prec) {
@@ -991,14 +1075,13 @@ static fe_status with_inner_type(int prec, F&& f) {
 }
 
 static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec, int max_cta, Workspace& w) {
-    const bool fp64 = prec == FE_PREC_FP64;
     const size_t esz = inner_bytes(prec);  // inner-precision vectors (uM, w)
     const size_t nv = (size_t)n_dof * R;
     for (auto pr : {std::make_pair(&w.b, nv * sizeof(double2)), std::make_pair(&w.x, nv * sizeof(double2)),
                     std::make_pair(&w.r, nv * sizeof(double2)), std::make_pair(&w.u, nv * sizeof(double2)),
                     std::make_pair(&w.p, nv * sizeof(double2)), std::make_pair(&w.s, nv * sizeof(double2)),
-                    std::make_pair(&w.uM, fp64 ? (size_t)16 : nv * esz),
-                    std::make_pair(&w.pM, fp64 ? (size_t)16 : nv * esz), std::make_pair(&w.w, nv * esz),
+                    std::make_pair(&w.uM, split_copies(prec, R) ? nv * esz : (size_t)16),
+                    std::make_pair(&w.pM, split_copies(prec, R) ? nv * esz : (size_t)16), std::make_pair(&w.w, nv * esz),
                     std::make_pair(&w.partial, (size_t)max_cta * kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.result, (size_t)kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.sync, sizeof(SyncState)),
@@ -1014,10 +1097,9 @@ static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec
 
 // Bytes alloc_workspace takes (before allocator rounding).
 size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta) {
-    const bool fp64 = prec == FE_PREC_FP64;
     const size_t nv = (size_t)n_dof * R;
     const size_t esz = inner_bytes(prec);
-    return nv * (6 * sizeof(double2) + (fp64 ? 1 : 3) * esz) + (size_t)(max_cta + 1) * kMaxNV * R * sizeof(double) +
+    return nv * (6 * sizeof(double2) + (split_copies(prec, R) ? 3 : 1) * esz) + (size_t)(max_cta + 1) * kMaxNV * R * sizeof(double) +
            (size_t)R * 32 + 4096;
 }
 
@@ -1036,6 +1118,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.valM = inner_matrix(s, prec);
     P.stride = s->stride;
     P.dinv64 = (const double2*)s->dinv64.ptr;
+    P.dinvdf = (const float4*)s->dinvdf.ptr;
     // class stencils and cost-balanced product ranges pay off for the
     // complex64 and FP32-pair products; the FP64 products stay explicit and
     // uniform
@@ -1052,8 +1135,11 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.u = (double2*)w.u.ptr;
     P.p = (double2*)w.p.ptr;
     P.s = (double2*)w.s.ptr;
-    P.uM = fp64 ? w.u.ptr : w.uM.ptr;
-    P.pM = fp64 ? w.p.ptr : w.pM.ptr;
+    // FP64 vectors, and FP32-pair vectors (FE_PREC_DF with R > 1), feed the
+    // products directly
+    const bool direct = fp64 || (df && R > 1);
+    P.uM = direct ? w.u.ptr : w.uM.ptr;
+    P.pM = direct ? w.p.ptr : w.pM.ptr;
     P.w = w.w.ptr;
     P.trace = (unsigned long long*)w.trace.ptr;
     // lexicographic node ranks: a neighbour is at most one plane, one line
@@ -1453,7 +1539,7 @@ void fe_solve_opts_default(fe_solve_opts* o) {
     o->precision = FE_PREC_DF;
     o->tol = 1e-8;
     o->reliable = 1e-4;
-    o->max_iter = 20000;
+    o->max_iter = 100000;
     o->max_outer = 200;
     o->rhs_tile = 0;
     o->max_pass_iter = 2000;
@@ -1614,7 +1700,7 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     take(w.p, nv * sizeof(double2));
     take(w.s, nv * sizeof(double2));
     take(w.w, nv * esz);
-    if (prec == FE_PREC_FP64) {
+    if (!split_copies(prec, R)) {
         w.uM = w.u;
         w.pM = w.p;
     } else {

@@ -84,7 +84,7 @@ class fe_solve_report(C.Structure):
 class fe_serve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("hbm_budget", C.c_int64),
-                ("max_ctas", C.c_int32), ("work_per_cta", C.c_int32)]
+                ("max_ctas", C.c_int32), ("work_per_cta", C.c_int32), ("max_job_ctas", C.c_int32)]
 
 
 class fe_request(C.Structure):
@@ -150,7 +150,7 @@ def load() -> C.CDLL:
         "fe_serve_info": (C.c_int, [P, C.POINTER(fe_serve_stats)]),
         "fe_serve_destroy": (None, [P]),
         "fe_serve_plan": (C.c_int32, [C.c_int32, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int32,
-                                      C.c_int32, C.POINTER(C.c_int32)]),
+                                      C.c_int32, C.c_int32, C.POINTER(C.c_int32)]),
         "fe_last_error": (C.c_char_p, []),
         "fe_launch_count": (C.c_int64, []),
     }
@@ -351,7 +351,7 @@ def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
     _check(load().fe_spmv(ctx, system, int(precision), int(nrhs), _ptr(x), _ptr(y)), "fe_spmv")
 
 
-def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
+def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
                rhs_tile=0, max_pass_iter=None) -> fe_solve_opts:
     o = fe_solve_opts()
     load().fe_solve_opts_default(C.byref(o))
@@ -416,13 +416,14 @@ def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_op
 
 # --------------------------------------------------------------------------
 # Serving
-def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=20000, max_outer=200,
-               hbm_budget=0, max_ctas=0, work_per_cta=0) -> fe_serve_opts:
+def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
+               hbm_budget=0, max_ctas=0, work_per_cta=0, max_job_ctas=0) -> fe_serve_opts:
     o = fe_serve_opts()
     load().fe_serve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
     o.max_iter, o.max_outer, o.hbm_budget = int(max_iter), int(max_outer), int(hbm_budget)
     o.max_ctas = int(max_ctas)
+    o.max_job_ctas = int(max_job_ctas)
     if work_per_cta:
         o.work_per_cta = int(work_per_cta)
     return o
@@ -471,7 +472,7 @@ def _result_dict(res: fe_result, copy: bool) -> dict:
         out["x"] = flat.view(np.complex128).reshape(res.n_dof, res.nrhs)
     if copy and res.node_id and res.n_dof:
         out["node_id"] = np.ctypeslib.as_array(res.node_id, shape=(res.n_dof // 3,)).copy()
-    if copy and res.reports:
+    if res.reports:  # small: always copied
         out["reports"] = _reports([res.reports[i] for i in range(res.nrhs)])
     return out
 
@@ -505,12 +506,13 @@ def fe_serve_destroy(server):
     load().fe_serve_destroy(server)
 
 
-def fe_serve_plan(rows, widths, max_ctas: int, work_per_cta: int) -> tuple[int, np.ndarray]:
+def fe_serve_plan(rows, widths, max_ctas: int, work_per_cta: int, max_job_ctas: int = 0) -> tuple[int, np.ndarray]:
     """The server's packing rule (host only): returns (taken, n_cta per request)."""
     r = np.ascontiguousarray(rows, dtype=np.int64)
     w = np.ascontiguousarray(widths, dtype=np.int32)
     out = np.zeros(r.size, np.int32)
     taken = load().fe_serve_plan(int(r.size), r.ctypes.data_as(C.POINTER(C.c_int64)),
-                                 w.ctypes.data_as(C.POINTER(C.c_int32)), int(max_ctas), int(work_per_cta),
+                                 w.ctypes.data_as(C.POINTER(C.c_int32)), int(max_ctas), int(max_job_ctas),
+                                 int(work_per_cta),
                                  out.ctypes.data_as(C.POINTER(C.c_int32)))
     return int(taken), out

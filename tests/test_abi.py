@@ -38,7 +38,7 @@ def test_option_defaults_without_gpu(fe):
     import ctypes
     o = fe.fe_solve_opts()
     fe.load().fe_solve_opts_default(ctypes.byref(o))
-    assert o.precision == fe.FE_PREC_DF and o.tol == 1e-8 and o.max_iter == 20000 and o.max_pass_iter == 2000
+    assert o.precision == fe.FE_PREC_DF and o.tol == 1e-8 and o.max_iter == 100000 and o.max_pass_iter == 2000
     s = fe.fe_serve_opts()
     fe.load().fe_serve_opts_default(ctypes.byref(s))
     assert s.precision == fe.FE_PREC_DF and s.tol == 1e-8 and s.work_per_cta == 2048
