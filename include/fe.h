@@ -235,6 +235,9 @@ typedef struct fe_solve_opts {
     int32_t max_pass_iter; /* mixed mode: a complex64 pass that has not dropped by `reliable` after this
                               many iterations is replaced all the same (its recursion has stalled);
                               0 = no cap; default 2000 */
+    int32_t wait_timeout_us; /* bound on every device-side wait of the solve (grid barriers, copy
+                              completions); on expiry the solve ends with FE_ERR_TIMEOUT and the
+                              context stays usable; 0 = default 4 000 000 (4 s) */
 } fe_solve_opts;
 
 void fe_solve_opts_default(fe_solve_opts* o);

@@ -244,7 +244,8 @@ __device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int
     const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns)) != 0;
     if (!ok) {
         atomicCAS(&P.sync->err, 0, kDevTimeout);
-        mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns);  // let the copy land before leaving
+        // let the copy land before the CTA leaves (its shared memory is the destination)
+        mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns > 2000000000ull ? P.timeout_ns : 2000000000ull);
     }
     phase += 1;
     shift = (int)((b0 - a0) / sizeof(C)) - 3 * h0 * R;
@@ -1162,7 +1163,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.rep_iters = ri + R;
     P.rep_outer = ri + 2 * R;
     P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
-    P.timeout_ns = 4000000000ull;
+    P.timeout_ns = 1000ull * (unsigned long long)(o.wait_timeout_us > 0 ? o.wait_timeout_us : 4000000);
     P.spin_ns = getenv("FE_SPIN_NS") ? (unsigned)atoi(getenv("FE_SPIN_NS")) : 0u;
 }
 
@@ -1521,7 +1522,7 @@ static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
         return FE_ERR_INVALID_ARG;
     }
     if (!(out.tol > 0.0) || out.max_iter < 1 || out.max_outer < 1 || !(out.reliable >= 0.0 && out.reliable < 1.0) ||
-        out.rhs_tile < 0 || out.max_pass_iter < 0) {
+        out.rhs_tile < 0 || out.max_pass_iter < 0 || out.wait_timeout_us < 0) {
         set_error("solve: bad tolerance or iteration limits");
         return FE_ERR_INVALID_ARG;
     }
@@ -1543,6 +1544,7 @@ void fe_solve_opts_default(fe_solve_opts* o) {
     o->max_outer = 200;
     o->rhs_tile = 0;
     o->max_pass_iter = 2000;
+    o->wait_timeout_us = 4000000;
 }
 
 fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y) {

@@ -68,7 +68,7 @@ class fe_planewave(C.Structure):
 class fe_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32),
-                ("max_pass_iter", C.c_int32)]
+                ("max_pass_iter", C.c_int32), ("wait_timeout_us", C.c_int32)]
 
 
 class fe_solve_stats(C.Structure):
@@ -352,13 +352,15 @@ def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
 
 
 def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
-               rhs_tile=0, max_pass_iter=None) -> fe_solve_opts:
+               rhs_tile=0, max_pass_iter=None, wait_timeout_us=None) -> fe_solve_opts:
     o = fe_solve_opts()
     load().fe_solve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
     o.max_iter, o.max_outer, o.rhs_tile = int(max_iter), int(max_outer), int(rhs_tile)
     if max_pass_iter is not None:
         o.max_pass_iter = int(max_pass_iter)
+    if wait_timeout_us is not None:
+        o.wait_timeout_us = int(wait_timeout_us)
     return o
 
 
