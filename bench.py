@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--requests", type=int, default=32,
                     help="config5: requests in the serving stream, its first ones (the full stream has 512)")
     ap.add_argument("--serve-precision", default="df", choices=["df", "fp64", "mixed"])
+    ap.add_argument("--kernel", default="solve", choices=["solve", "spmv"],
+                    help="spmv: time the standalone sparse product fe_spmv instead of the solve")
     return ap.parse_args()
 
 
@@ -369,6 +371,88 @@ def run_ours(args, rank, world, local_rank, precision_name):
     return line
 
 
+def run_spmv(args, rank, world, local_rank):
+    """Standalone sparse products y = A x (fe_spmv) on the workload's matrix in
+    each precision, R = 1, 8 and 16 columns.  Algorithmic bytes per product
+    (s = bytes of one entry: complex64 8, complex128 and FP32 pairs 16):
+    nnzb*(9*s + 4) + (n_nodes + 1)*4 + 2*n_dof*R*s.  Every timed product is
+    preceded by a 512 MiB write that flushes L2 and is timed alone with CUDA
+    events on the context stream."""
+    import numpy as np
+    import torch
+
+    from paper_0704_2344_gb300 import build, fe
+    build.build()
+    torch.cuda.set_device(local_rank)
+    prob, _ = workload(args.workload)
+    stream = torch.cuda.Stream()
+    ctx = fe.fe_ctx_create(local_rank, stream=stream.cuda_stream)
+    dev = f"cuda:{local_rank}"
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    mesh = fe.fe_mesh_create_from(ctx, prob)
+    info = fe.fe_mesh_info(mesh)
+    nnzb, n, n_dof = info["nnzb"], info["n_nodes"], info["n_dof"]
+    peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    table = {}
+    launches0 = fe.fe_launch_count()
+    n_timed = 0
+    with ClockSampler(local_rank) as clk:
+        for pname, prec, esz in (("mixed", fe.FE_PREC_MIXED, 8), ("fp64", fe.FE_PREC_FP64, 16),
+                                 ("df", fe.FE_PREC_DF, 16)):
+            system = fe.fe_assemble(ctx, mesh, prob.freq_hz, prec)
+            try:
+                for R in (1, 8, 16):
+                    with torch.cuda.stream(stream):
+                        if pname == "mixed":
+                            x = torch.randn(n_dof, R, dtype=torch.complex64, device=dev)
+                        elif pname == "fp64":
+                            x = torch.randn(n_dof, R, dtype=torch.complex128, device=dev)
+                        else:
+                            x = torch.randn(n_dof, R, 4, dtype=torch.float32, device=dev)
+                            x[..., 2:] *= 2.0 ** -24  # a valid low part
+                        y = torch.empty_like(x)
+                    stream.synchronize()
+                    for _ in range(max(3, args.warmup)):
+                        fe.fe_spmv(ctx, system, prec, R, x, y)
+                    times = []
+                    for _ in range(args.steps):
+                        with torch.cuda.stream(stream):
+                            flush.fill_(1)
+                            e0 = torch.cuda.Event(enable_timing=True)
+                            e1 = torch.cuda.Event(enable_timing=True)
+                            e0.record(stream)
+                        fe.fe_spmv(ctx, system, prec, R, x, y)
+                        with torch.cuda.stream(stream):
+                            e1.record(stream)
+                        stream.synchronize()
+                        times.append(e0.elapsed_time(e1))
+                        n_timed += 1
+                    ms = statistics.median(times)
+                    by = nnzb * (9 * esz + 4) + (n + 1) * 4 + 2 * n_dof * R * esz
+                    fl = (60 if pname == "df" else 8) * 9.0 * nnzb * R
+                    table[f"{pname}_R{R}"] = {"ms": round(ms, 4), "gbs": round(by / ms / 1e6, 1),
+                                             "frac_hbm": round(by / ms / 1e6 / hbm_peak, 4),
+                                             "tflops": round(fl / ms / 1e9, 3), "bytes": int(by)}
+            finally:
+                fe.fe_system_destroy(system)
+    fe.fe_mesh_destroy(mesh)
+    fe.fe_ctx_destroy(ctx)
+    head = table["mixed_R1"]
+    return {
+        "metric": "SpMV HBM GB/s (algorithmic bytes)", "value": head["gbs"], "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": head["ms"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {prob.name}, {n_dof} unknowns, {nnzb} blocks",
+                   "l2": "512 MiB flush before every timed product", "parallelism": f"replicas x{world}"},
+        "roofline": {"kernel": "k_spmv_r1<float2> (warp per block row, lane per block)", "bound": "hbm",
+                     "achieved": head["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": head["frac_hbm"],
+                     "traffic": None, "algorithmic_bytes_per_launch": head["bytes"]},
+        "table": table, "gpu_launches": fe.fe_launch_count() - launches0, "timed_launches": n_timed,
+        "e2e": None, "clocks": clk.summary(),
+    }
+
+
 def run_serving(args, rank, world, local_rank):
     """Serving stream (config5): independent cubes of 8^3..50^3 nodes
     (log-uniform), 1-6 GHz at lambda/10, a random PEC box, 1-16 plane waves.
@@ -602,6 +686,11 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
+    if args.kernel == "spmv":
+        line = run_spmv(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
     if args.workload == "config5":
         line = run_serving(args, rank, world, local_rank)
         if rank == 0:
