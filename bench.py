@@ -445,7 +445,7 @@ def run_spmv(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {prob.name}, {n_dof} unknowns, {nnzb} blocks",
                    "l2": "512 MiB flush before every timed product", "parallelism": f"replicas x{world}"},
-        "roofline": {"kernel": "k_spmv_r1<float2> (warp per block row, lane per block)", "bound": "hbm",
+        "roofline": {"kernel": "k_spmv_warp<float2> (warp per block row, lane per block)", "bound": "hbm",
                      "achieved": head["gbs"], "peak": hbm_peak, "unit": "GB/s", "frac": head["frac_hbm"],
                      "traffic": None, "algorithmic_bytes_per_launch": head["bytes"]},
         "table": table, "gpu_launches": fe.fe_launch_count() - launches0, "timed_launches": n_timed,

@@ -69,6 +69,16 @@ __device__ __forceinline__ void dfc_mac4(float* acc, const float4& m, const floa
     df_mac(acc[2], acc[3], m.y, m.w, x.x, x.z);
 }
 
+// (h, l) += (h2, l2): TwoSum of the high parts, the error and both low parts
+// into l.
+__device__ __forceinline__ void df_add(float& h, float& l, float h2, float l2) {
+    const float t = __fadd_rn(h, h2);
+    const float v = __fsub_rn(t, h);
+    const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(t, v)), __fsub_rn(h2, v));
+    h = t;
+    l = __fadd_rn(l, __fadd_rn(l2, e));
+}
+
 // Canonical pair of h + l (TwoSum: h = RN(h + l), l = the exact remainder).
 __device__ __forceinline__ void df_norm(float& h, float& l) {
     const float t = __fadd_rn(h, l);
@@ -163,51 +173,6 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, unsigned parit
 // acquired from other threads) before its later async-proxy (bulk copy)
 // accesses, for global and shared memory.
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async;" ::: "memory"); }
-
-// Row product for a single vector (block values in 9 planes of `stride`
-// entries): lane l < nb = s1 - s0 owns block s0 + l
-// (column index `mycol`, loaded by the caller, possibly one row ahead): it
-// loads the block's 9 complex entries and the 3 entries of x at its column,
-// accumulates the 3x3 block product into fixed accumulators, and a butterfly
-// over the warp adds the blocks of the row.  `xs` is indexed by vector entry
-// minus `xoff` (a shared-memory halo copy, or global memory with xoff = 0).
-template <typename C, bool kShared>
-__device__ __forceinline__ void row_product_r1x(const C* __restrict__ val, int64_t stride, int mycol, int s0, int s1,
-                                                const C* xs, int xoff, int lane, C& y0, C& y1, C& y2) {
-    using Tr = decltype(C{}.x);
-    Tr a0r = 0, a0i = 0, a1r = 0, a1i = 0, a2r = 0, a2i = 0;
-    if (lane < s1 - s0) {
-        const C* v = val + s0 + lane;  // plane q at v + q * stride: consecutive lanes, consecutive blocks
-        C m[9];
-#pragma unroll
-        for (int q = 0; q < 9; ++q) m[q] = ld_ro(v + q * stride);
-        const int xi = 3 * mycol - xoff;
-        C x[3];
-#pragma unroll
-        for (int be = 0; be < 3; ++be) x[be] = kShared ? xs[xi + be] : ld_cg(xs + xi + be);
-#pragma unroll
-        for (int be = 0; be < 3; ++be) {
-            a0r += m[be].x * x[be].x - m[be].y * x[be].y;
-            a0i += m[be].x * x[be].y + m[be].y * x[be].x;
-            a1r += m[3 + be].x * x[be].x - m[3 + be].y * x[be].y;
-            a1i += m[3 + be].x * x[be].y + m[3 + be].y * x[be].x;
-            a2r += m[6 + be].x * x[be].x - m[6 + be].y * x[be].y;
-            a2i += m[6 + be].x * x[be].y + m[6 + be].y * x[be].x;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        a0r += __shfl_xor_sync(0xffffffffu, a0r, o);
-        a0i += __shfl_xor_sync(0xffffffffu, a0i, o);
-        a1r += __shfl_xor_sync(0xffffffffu, a1r, o);
-        a1i += __shfl_xor_sync(0xffffffffu, a1i, o);
-        a2r += __shfl_xor_sync(0xffffffffu, a2r, o);
-        a2i += __shfl_xor_sync(0xffffffffu, a2i, o);
-    }
-    y0 = mk(a0r, a0i);
-    y1 = mk(a1r, a1i);
-    y2 = mk(a2r, a2i);
-}
 
 // FP64 reciprocal (CUDA's round-to-nearest intrinsic).
 __device__ __forceinline__ double rcp64(double x) { return __drcp_rn(x); }
