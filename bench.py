@@ -3,15 +3,23 @@
 
 One step = one pass of the whole path on one synthetic problem: device mesh
 and block pattern, assembly of Eq. 4 into 3x3-block rows (+ block-Jacobi
-inverse + complex64 copy), plane-wave right-hand side, and the mixed-precision
-COCG solve with FP64 refinement down to ||b - A x|| / ||b|| <= 1e-8.
-Default workload: the 3-wavelength cube (30^3 elements of lambda/10 at 3 GHz,
-centred 6^3 PEC cube, eps_r = 4 slab, 88 998 unknowns), one plane wave.
+inverse + the inner-precision copy), plane-wave right-hand side, and the
+persistent COCG solve down to ||b - A x|| / ||b|| <= 1e-8 (FP64 true
+residual).  Default workload: the 3-wavelength cube (30^3 elements of
+lambda/10 at 3 GHz, centred 6^3 PEC cube, eps_r = 4 slab, 88 998 unknowns),
+one plane wave.  --precision auto (default) times the three precisions (FP64;
+complex64 products in FP64 refinement; FP32-pair products) and reports the
+fastest one that converged, with the others under "modes".
 
 `value` times steps with inputs resident in HBM (material grid on the device,
 solution left on the device); `e2e` runs the same steps through the public
 API with host buffers (host material grid in, host solution out).  Between
 timed steps a 512 MiB buffer is written to flush the 126 MB L2.
+
+Other modes: --workload config1..4 (larger or batched solves), --workload
+config5 (a serving stream through fe_serve_*, against sequential FP64
+solves), --kernel spmv (the standalone sparse product fe_spmv, GB/s of
+algorithmic bytes).
 
 --impl reference times the FP64 CPU oracle on the host cores (bounded sample,
 see cpu_baseline).  Under torchrun every rank solves its own copy of the
