@@ -192,7 +192,7 @@ def kernel_hash() -> str:
     import hashlib
     csrc = ROOT / "paper_0704_2344_gb300" / "csrc"
     h = hashlib.sha256()
-    for f in ("solve.cu", "krylov.cuh", "fe_internal.cuh"):
+    for f in ("solve.cu", "solve_kernels.cuh", "krylov.cuh", "fe_internal.cuh"):
         h.update((csrc / f).read_bytes())
     return h.hexdigest()[:16]
 

@@ -1,0 +1,174 @@
+// Standalone sparse products y = A x (fe_spmv): the Krylov loop's product
+// (Section 3.1.5.1) as its own entry point, for one or several vectors.
+#include "krylov.cuh"
+
+#include <algorithm>
+#include <type_traits>
+
+namespace fe {
+
+template <typename C>
+__global__ void __launch_bounds__(256) k_spmv_cols(const C* __restrict__ val, int64_t stride,
+                                                   const int* __restrict__ col, const int* __restrict__ rp,
+                                                   const C* __restrict__ x, C* __restrict__ y, int n_rows, int nrhs) {
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (int64_t)n_rows * nrhs) return;
+    const int row = (int)(t / nrhs), c = (int)(t - (int64_t)row * nrhs);
+    C v[3];
+    row_product_colx<C, false>(val, stride, col, __ldg(rp + row), __ldg(rp + row + 1), x, 0, nrhs, c, v[0], v[1],
+                               v[2]);
+#pragma unroll
+    for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * nrhs + c] = v[al];
+}
+
+// y = A x for R = 1, 2, 4, ..., 32 columns: one warp per block row, its lanes
+// split into 32/R block groups x R columns.  A block's nine entries are read
+// once per warp (the R lanes of a group read the same address), the R values
+// of one vector entry are contiguous, and the groups' partial sums meet in a
+// shuffle reduction (FP32 pairs: error-free pair additions).
+template <typename C, int R>
+__global__ void __launch_bounds__(256) k_spmv_warp(const C* __restrict__ val, int64_t stride,
+                                                   const int* __restrict__ col, const int* __restrict__ rp,
+                                                   const C* __restrict__ x, C* __restrict__ y, int n_rows) {
+    const int lane = threadIdx.x & 31;
+    constexpr int G = 32 / R;
+    const int c = lane % R, g = lane / R;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int row = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; row < n_rows; row += nw) {
+        const int s0 = __ldg(rp + row), s1 = __ldg(rp + row + 1);
+        // the nine entries of a block load before its (dependent) vector entries;
+        // the next column index loads one step ahead
+        int cb = s0 + g < s1 ? __ldg(col + s0 + g) : 0;
+        if constexpr (std::is_same<C, float4>::value) {
+            float a[3][4] = {};
+            for (int s = s0 + g; s < s1; s += G) {
+                const int cb_next = s + G < s1 ? __ldg(col + s + G) : 0;
+                float4 m[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) m[q] = __ldg(val + q * stride + s);
+                const int xb = 3 * cb * R + c;
+                float4 xv[3];
+#pragma unroll
+                for (int be = 0; be < 3; ++be) xv[be] = __ldg(x + xb + be * R);
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) dfc_mac(a[al], m[3 * al + be], xv[be]);
+                cb = cb_next;
+            }
+#pragma unroll
+            for (int o = 16; o >= R; o >>= 1)
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int q = 0; q < 4; q += 2) {
+                        const float h2 = __shfl_xor_sync(0xffffffffu, a[al][q], o);
+                        const float l2 = __shfl_xor_sync(0xffffffffu, a[al][q + 1], o);
+                        df_add(a[al][q], a[al][q + 1], h2, l2);
+                    }
+            if (g == 0)
+#pragma unroll
+                for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * R + c] = df_result_norm(a[al]);
+        } else {
+            using Tr = decltype(C{}.x);
+            Tr a[6] = {0, 0, 0, 0, 0, 0};
+            for (int s = s0 + g; s < s1; s += G) {
+                const int cb_next = s + G < s1 ? __ldg(col + s + G) : 0;
+                C m[9];
+#pragma unroll
+                for (int q = 0; q < 9; ++q) m[q] = __ldg(val + q * stride + s);
+                const int xb = 3 * cb * R + c;
+                C xv[3];
+#pragma unroll
+                for (int be = 0; be < 3; ++be) xv[be] = __ldg(x + xb + be * R);
+#pragma unroll
+                for (int al = 0; al < 3; ++al)
+#pragma unroll
+                    for (int be = 0; be < 3; ++be) {
+                        a[2 * al] += m[3 * al + be].x * xv[be].x - m[3 * al + be].y * xv[be].y;
+                        a[2 * al + 1] += m[3 * al + be].x * xv[be].y + m[3 * al + be].y * xv[be].x;
+                    }
+                cb = cb_next;
+            }
+#pragma unroll
+            for (int o = 16; o >= R; o >>= 1)
+#pragma unroll
+                for (int k = 0; k < 6; ++k) a[k] += __shfl_xor_sync(0xffffffffu, a[k], o);
+            if (g == 0)
+#pragma unroll
+                for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * R + c] = mk(a[2 * al], a[2 * al + 1]);
+        }
+    }
+}
+
+template <typename C>
+static void launch_spmv_warp(int R, unsigned blocks, cudaStream_t st, const C* val, int64_t stride, const int* col,
+                             const int* rp, const C* x, C* y, int n_rows) {
+    switch (R) {
+        case 1: k_spmv_warp<C, 1><<<blocks, 256, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        case 2: k_spmv_warp<C, 2><<<blocks, 256, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        case 4: k_spmv_warp<C, 4><<<blocks, 256, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        case 8: k_spmv_warp<C, 8><<<blocks, 256, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        case 16: k_spmv_warp<C, 16><<<blocks, 256, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        default: k_spmv_warp<C, 32><<<blocks, 256, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+    }
+}
+
+}  // namespace fe
+
+using namespace fe;
+
+extern "C" {
+
+fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y) {
+    if (!ctx || !s || !x || !y || nrhs < 1) {
+        set_error("fe_spmv: NULL argument or nrhs < 1");
+        return FE_ERR_INVALID_ARG;
+    }
+    const fe_mesh* m = s->mesh;
+    cudaStream_t st = ctx->stream;
+    const int* rp = (const int*)m->row_ptr.ptr;
+    const int* col = (const int*)m->col_idx.ptr;
+    const bool pow2 = nrhs <= 32 && (nrhs & (nrhs - 1)) == 0;
+    const unsigned warp_blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 8,
+                                                                                  ((int64_t)m->n_act + 7) / 8));
+    const int64_t n_items = (int64_t)m->n_act * nrhs;
+    const unsigned col_blocks = (unsigned)((n_items + 255) / 256);
+    if (precision == FE_PREC_FP64) {
+        if (pow2)
+            launch_spmv_warp<double2>(nrhs, warp_blocks, st, (const double2*)s->val64.ptr, s->stride, col, rp,
+                                  (const double2*)x, (double2*)y, m->n_act);
+        else
+            k_spmv_cols<double2><<<col_blocks, 256, 0, st>>>((const double2*)s->val64.ptr, s->stride, col, rp,
+                                                             (const double2*)x, (double2*)y, m->n_act, nrhs);
+    } else if (precision == FE_PREC_MIXED) {
+        if (!s->val32.ptr) {
+            set_error("fe_spmv: no complex64 copy (system assembled in FP64)");
+            return FE_ERR_INVALID_ARG;
+        }
+        if (pow2)
+            launch_spmv_warp<float2>(nrhs, warp_blocks, st, (const float2*)s->val32.ptr, s->stride, col, rp,
+                                  (const float2*)x, (float2*)y, m->n_act);
+        else
+            k_spmv_cols<float2><<<col_blocks, 256, 0, st>>>((const float2*)s->val32.ptr, s->stride, col, rp,
+                                                            (const float2*)x, (float2*)y, m->n_act, nrhs);
+    } else if (precision == FE_PREC_DF) {
+        if (!s->valdf.ptr) {
+            set_error("fe_spmv: no FP32-pair copy (system not assembled with FE_PREC_DF)");
+            return FE_ERR_INVALID_ARG;
+        }
+        if (pow2)
+            launch_spmv_warp<float4>(nrhs, warp_blocks, st, (const float4*)s->valdf.ptr, s->stride, col, rp,
+                                  (const float4*)x, (float4*)y, m->n_act);
+        else
+            k_spmv_cols<float4><<<col_blocks, 256, 0, st>>>((const float4*)s->valdf.ptr, s->stride, col, rp,
+                                                            (const float4*)x, (float4*)y, m->n_act, nrhs);
+    } else {
+        set_error("fe_spmv: bad precision");
+        return FE_ERR_INVALID_ARG;
+    }
+    FE_LAUNCHED();
+    return FE_OK;
+}
+
+}  // extern "C"
