@@ -57,6 +57,11 @@ def parse():
     ap.add_argument("--requests", type=int, default=32,
                     help="config5: requests in the serving stream, its first ones (the full stream has 512)")
     ap.add_argument("--serve-precision", default="df", choices=["df", "fp64", "mixed"])
+    ap.add_argument("--serve-only", action="store_true",
+                    help="config5: only the all-at-t=0 serving pass (no sequential baseline, no Poisson pass)")
+    ap.add_argument("--max-job-ctas", type=int, default=0, help="config5: CTAs one request may take (0: default)")
+    ap.add_argument("--rhs-tile", type=int, default=0,
+                    help="right-hand sides per persistent launch (0: the library's choice)")
     ap.add_argument("--kernel", default="solve", choices=["solve", "spmv"],
                     help="spmv: time the standalone sparse product fe_spmv instead of the solve")
     return ap.parse_args()
@@ -229,7 +234,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
     precision = {"mixed": fe.FE_PREC_MIXED, "fp64": fe.FE_PREC_FP64, "df": fe.FE_PREC_DF}[precision_name]
     stream = torch.cuda.Stream()
     ctx = fe.fe_ctx_create(local_rank, stream=stream.cuda_stream)
-    opts = fe.solve_opts(precision=precision, tol=1e-8)
+    opts = fe.solve_opts(precision=precision, tol=1e-8, rhs_tile=args.rhs_tile)
     mat_d = torch.from_numpy(np.ascontiguousarray(prob.material).ravel()).to(f"cuda:{local_rank}")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
     R = waves.count
@@ -363,6 +368,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {prob.name}, {info['n_dof']} unknowns, {R} plane wave(s)",
                    "n_dof": info["n_dof"], "nnzb": info["nnzb"], "rhs": R, "precision": precision_name,
+                   "rhs_tile": args.rhs_tile or "auto",
                    "tol": 1e-8, "l2": "512 MiB flush between timed steps", "parallelism": f"replicas x{world}"},
         "converged": ok,
         "iterations_per_solve": inner_iters / (args.steps * R),
@@ -503,7 +509,7 @@ def run_serving(args, rank, world, local_rank):
             fe.fe_mesh_destroy(mesh)
 
     def serve(arrivals):
-        srv = fe.fe_serve_create(ctx, fe.serve_opts(precision=prec))
+        srv = fe.fe_serve_create(ctx, fe.serve_opts(precision=prec, max_job_ctas=args.max_job_ctas))
         try:
             t0 = time.perf_counter()
             tickets = []
@@ -532,11 +538,11 @@ def run_serving(args, rank, world, local_rank):
     t0 = time.perf_counter()
     seq_ok = 0
     seq_times = []
-    for q in reqs:
+    for q in ([] if args.serve_only else reqs):
         ts = time.perf_counter()
         seq_ok += bool(sequential(q))
         seq_times.append(time.perf_counter() - ts)
-    seq_wall = time.perf_counter() - t0
+    seq_wall = time.perf_counter() - t0 if seq_times else float("nan")
     print(f"config5: sequential FP64 {len(reqs)} requests in {seq_wall:.1f} s ({seq_ok} converged)", file=sys.stderr,
           flush=True)
 
@@ -556,12 +562,17 @@ def run_serving(args, rank, world, local_rank):
     print(f"config5: served all at t=0 in {wall:.1f} s ({ok} converged, {info['launches']} launches)",
           file=sys.stderr, flush=True)
 
-    rng = np.random.default_rng(20070704 + 55 + rank)
-    gaps = rng.exponential(1.25 * float(np.mean(seq_times)), len(reqs))
-    arrivals = np.concatenate([[0.0], np.cumsum(gaps)[:-1]])
-    lat_wall, lat_res, lat_info = serve(list(arrivals))
-    lat = np.array([r["t_done"] - r["t_submit"] for r in lat_res])
-    seq_lat = np.array(seq_times)
+    if args.serve_only:
+        lat_wall, lat_res, lat_info = float("nan"), res, info
+        lat = np.array([r["t_done"] - r["t_submit"] for r in res])
+        seq_lat = np.array([float("nan")])
+    else:
+        rng = np.random.default_rng(20070704 + 55 + rank)
+        gaps = rng.exponential(1.25 * float(np.mean(seq_times)), len(reqs))
+        arrivals = np.concatenate([[0.0], np.cumsum(gaps)[:-1]])
+        lat_wall, lat_res, lat_info = serve(list(arrivals))
+        lat = np.array([r["t_done"] - r["t_submit"] for r in lat_res])
+        seq_lat = np.array(seq_times)
 
     vals = torch.tensor([wall, seq_wall, lat_wall], dtype=torch.float64, device=f"cuda:{local_rank}")
     if world > 1:
@@ -576,7 +587,7 @@ def run_serving(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"config5: serving stream of {args.requests} cubes 8^3..50^3 nodes, 1-16 plane waves",
                    "requests_per_rank": len(reqs), "rhs_per_rank": n_solves, "grid_dof_per_rank": n_dof_total,
-                   "serve_precision": args.serve_precision, "tol": 1e-8,
+                   "serve_precision": args.serve_precision, "tol": 1e-8, "max_job_ctas": args.max_job_ctas or "default",
                    "l2": "inputs of successive requests differ; no flush", "parallelism": f"replicas x{world}"},
         "served_ok": ok, "sequential_ok": seq_ok,
         "served_failed": failed, "served_slowest": [describe(i, res[i]) for i in reversed(slowest)],
@@ -585,7 +596,8 @@ def run_serving(args, rank, world, local_rank):
                             "p50_s": round(float(np.percentile(seq_lat, 50)), 5),
                             "p99_s": round(float(np.percentile(seq_lat, 99)), 5)},
         "speedup_vs_sequential_fp64": round(seq_wall / wall, 3),
-        "latency": {"arrival": "poisson", "mean_gap_s": round(1.25 * float(np.mean(seq_times)), 5),
+        "latency": {"arrival": "all at t=0 (--serve-only)" if args.serve_only else "poisson",
+                    "mean_gap_s": round(1.25 * float(np.mean(seq_times)), 5) if seq_times else None,
                     "p50_s": round(float(np.percentile(lat, 50)), 5), "p99_s": round(float(np.percentile(lat, 99)), 5),
                     "max_s": round(float(lat.max()), 5), "wall_s": round(lat_wall, 3),
                     "ok": int(sum(r["status"] == fe.FE_OK for r in lat_res)),

@@ -316,8 +316,9 @@ typedef struct fe_serve_opts {
     int64_t hbm_budget;    /* device bytes for admitted requests; 0: 80 % of the free memory at creation */
     int32_t max_ctas;      /* CTAs of one launch, 1..one per SM; 0: one per SM */
     int32_t work_per_cta;  /* packing target, block rows x tile width per CTA; 0: 2048 */
-    int32_t max_job_ctas;  /* CTAs one request may take, so that a large request leaves room for others;
-                              0: half the SMs */
+    int32_t max_job_ctas;  /* CTAs one request may take (a cap leaves room for other requests beside a
+                              large one); 0: no cap.  On a stream of 8^3..50^3-node cubes no cap gave
+                              the highest throughput: the large requests scale across the device */
 } fe_serve_opts;
 void fe_serve_opts_default(fe_serve_opts* o);
 

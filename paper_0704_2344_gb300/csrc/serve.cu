@@ -205,7 +205,7 @@ bool worker_turn(fe_server* S) {
         width[i] = job_width(S->ready[i]->job);
     }
     const int max_ctas = S->o.max_ctas > 0 ? std::min(S->o.max_ctas, S->ictx->num_sms) : S->ictx->num_sms;
-    const int max_job = S->o.max_job_ctas > 0 ? std::min(S->o.max_job_ctas, max_ctas) : std::max(1, max_ctas / 2);
+    const int max_job = S->o.max_job_ctas > 0 ? std::min(S->o.max_job_ctas, max_ctas) : max_ctas;
     fe_serve_plan(n, rows.data(), width.data(), max_ctas, max_job, S->o.work_per_cta, n_cta.data());
     std::vector<ServeReq*> batch, rest;
     std::vector<SolveJob*> jobs;
