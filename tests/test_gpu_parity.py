@@ -301,6 +301,44 @@ def test_batched_columns_match_single_solves(fe, ctx):
         assert np.linalg.norm(xb[:, j] - xref[:, j]) <= 1e-6 * np.linalg.norm(xref[:, j])
 
 
+def test_batched_columns_match_single_solves_fp32_pairs(fe, ctx):
+    """Eight columns in one FE_PREC_DF launch keep their Krylov vectors as FP32
+    pairs; each column still meets the single-column FP64-recurrence solve
+    and the oracle's direct solution."""
+    prob = W.random_small_grid(6, n_max=7, n_pec_boxes=1)
+    waves = W.random_waves(8, np.random.default_rng(1))
+    maps = fem.mesh_maps(prob)
+    A = fem.assemble(prob, maps=maps)
+    B = fem.rhs(prob, waves, maps=maps)
+    xref = fem.solve_direct(A, B)
+    xb, repb = _solve(fe, ctx, prob, waves, fe.FE_PREC_DF)
+    assert all(r["status"] == 0 for r in repb)
+    assert fem.true_relative_residual(A, xb, B).max() <= 1e-8
+    for j in (0, 5):
+        xs, _ = _solve(fe, ctx, prob, waves.column(j), fe.FE_PREC_DF)
+        assert np.linalg.norm(xs[:, 0] - xb[:, j]) <= 1e-6 * np.linalg.norm(xref[:, j])
+    for j in range(8):
+        assert np.linalg.norm(xb[:, j] - xref[:, j]) <= 1e-6 * np.linalg.norm(xref[:, j])
+
+
+def test_solve_config2_32_waves_one_launch(fe, ctx, config2):
+    """The 3-wavelength cube at full size with 32 plane waves (the first 32 of
+    the 64-wave workload) in one 32-column FP32-pair launch: every column's
+    FP64 true residual, recomputed on the CPU with the oracle's matrix, is at
+    most 1e-8."""
+    prob, _, maps, A = config2
+    w64 = W.config3()[1]
+    waves = w64.__class__(w64.k_hat[:32], w64.p_hat[:32], w64.amplitude[:32])
+    x, rep = _solve(fe, ctx, prob, waves, fe.FE_PREC_DF)
+    stats = fe.fe_last_solve_stats(ctx)
+    assert stats["launches"] == 1 and stats["tile_width"] == 32
+    assert all(r["status"] == 0 for r in rep), rep
+    B = fem.rhs(prob, waves, maps=maps)
+    res = fem.true_relative_residual(A, x, B)
+    assert res.max() <= 1e-8, res.max()
+    assert np.allclose([r["rel_residual"] for r in rep], res, rtol=0, atol=1e-9)
+
+
 def test_mesh_errors(fe, ctx):
     p = W.empty_box(4)
     p.material[0, 1, 1] = 255
