@@ -227,7 +227,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
     import numpy as np
     import torch
 
-    from paper_0704_2344_gb300 import build, fe
+    from paper_0704_2344_gb300 import build, fe, replicas
     build.build()
     torch.cuda.set_device(local_rank)
     prob, waves = workload(args.workload)
@@ -269,8 +269,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
     for _ in range(args.warmup):
         step(True, x_dev=x_dev)
     torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     launches0 = fe.fe_launch_count()
     evs = []
@@ -292,8 +291,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
             passes += stats["passes"]
             statuses.append((st, [r["rel_residual"] for r in rep], [r["iterations"] for r in rep]))
         torch.cuda.synchronize()
-    if world > 1:
-        torch.distributed.barrier()
+    replicas.barrier()
     torch.cuda.synchronize()
     t_wall = time.perf_counter() - t_wall0
     launches = fe.fe_launch_count() - launches0
@@ -307,11 +305,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
         step(False, x_host=x_host)
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     ms_local = total_ms / args.steps
-    ms = ms_local
-    if world > 1:
-        t = torch.tensor([ms_local], device=f"cuda:{local_rank}", dtype=torch.float64)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks([ms_local], device=f"cuda:{local_rank}")[0]  # the slowest rank
     alg, inner_b, outer_b = algorithmic_bytes(info, sysinfo, precision_name, inner_iters / R, passes, R)
     fl_prod, fl64 = algorithmic_flops(info, sysinfo, precision_name, inner_iters / R, passes, R)
     launch_ms = kernel_ms / args.steps
@@ -484,11 +478,11 @@ def run_serving(args, rank, world, local_rank):
     import numpy as np
     import torch
 
-    from paper_0704_2344_gb300 import build, fe
+    from paper_0704_2344_gb300 import build, fe, replicas
     from paper_0704_2344_gb300 import workloads as W
     build.build()
     torch.cuda.set_device(local_rank)
-    reqs = W.config5(n_requests=args.requests)[rank::world]
+    reqs = replicas.shard(W.config5(n_requests=args.requests), rank, world)
     ctx = fe.fe_ctx_create(local_rank)
     prec = {"mixed": fe.FE_PREC_MIXED, "fp64": fe.FE_PREC_FP64, "df": fe.FE_PREC_DF}[args.serve_precision]
     n_solves = sum(q.waves.count for q in reqs)
@@ -574,11 +568,8 @@ def run_serving(args, rank, world, local_rank):
         lat = np.array([r["t_done"] - r["t_submit"] for r in lat_res])
         seq_lat = np.array(seq_times)
 
-    vals = torch.tensor([wall, seq_wall, lat_wall], dtype=torch.float64, device=f"cuda:{local_rank}")
-    if world > 1:
-        torch.distributed.all_reduce(vals, op=torch.distributed.ReduceOp.MAX)
-    wall, seq_wall, lat_wall = (float(v) for v in vals.cpu())
-    total_solves = n_solves * world  # every rank serves a share of the same size class
+    wall, seq_wall, lat_wall = replicas.max_over_ranks([wall, seq_wall, lat_wall], device=f"cuda:{local_rank}")
+    total_solves = int(replicas.sum_over_ranks([n_solves], device=f"cuda:{local_rank}")[0])
     value = round(total_solves / wall, 3)
     line = {
         "metric": "RHS solves/s at 1e-8 rel. residual", "value": value, "unit": "solves/s",
@@ -710,6 +701,9 @@ def main():
         line = run_spmv(args, rank, world, local_rank)
         if rank == 0:
             print(json.dumps(line), flush=True)
+        if world > 1:
+            import torch
+            torch.distributed.destroy_process_group()
         return
     if args.workload == "config5":
         line = run_serving(args, rank, world, local_rank)
