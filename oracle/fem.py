@@ -284,11 +284,12 @@ def mesh_maps(problem) -> Maps:
     dims = (nx, ny, nz)
     coords = (i, j, k)
     mflat = mat.ravel()
+    bnd = boundary_kinds(problem)
     for f in range(6):
         axis, side = f // 2, f % 2
         c = coords[axis]
         on_box = (c == 0) if side == 0 else (c == dims[axis] - 1)
-        ext_f = act_el.ravel() & on_box
+        ext_f = act_el.ravel() & on_box & (bnd[f] == 0)  # only absorbing faces are Sext
         ext.append(6 * np.flatnonzero(ext_f) + f)
         step = (1, nx, nx * ny)[axis] * (1 if side == 1 else -1)
         inside = act_el.ravel() & ~on_box
@@ -309,7 +310,39 @@ def mesh_maps(problem) -> Maps:
     m.faces_ext = np.sort(np.concatenate(ext))
     m.faces_pec = np.sort(np.concatenate(pec))
     m.n_dof = 3 * n_act
+    m.fixed = fixed_dofs(problem, m)
     return m
+
+
+def boundary_kinds(problem):
+    """Kind of each box face (-x, +x, -y, +y, -z, +z): 0 absorbing (Eq. 3),
+    1 symmetry plane (n . H = 0, Eq. 6a), 2 antisymmetry plane (n x H = 0,
+    Eq. 6b)."""
+    b = tuple(int(v) for v in getattr(problem, "boundary", (0,) * 6))
+    if len(b) != 6 or any(v not in (0, 1, 2) for v in b):
+        raise ValueError("boundary kinds are 0, 1 or 2 per face")
+    return b
+
+
+def fixed_dofs(problem, maps):
+    """Unknowns held at zero by symmetry planes: on a symmetry plane the
+    normal component of H (Eq. 6a), on an antisymmetry plane its two
+    tangential components (Eq. 6b)."""
+    bnd = boundary_kinds(problem)
+    nx, ny, nz = problem.nx, problem.ny, problem.nz
+    ids = np.flatnonzero(maps.node_active)
+    ijk = (ids % (nx + 1), (ids // (nx + 1)) % (ny + 1), ids // ((nx + 1) * (ny + 1)))
+    dims = (nx, ny, nz)
+    fixed = np.zeros((ids.size, 3), dtype=bool)
+    for f in range(6):
+        if bnd[f] == 0:
+            continue
+        axis, side = f // 2, f % 2
+        on = ijk[axis] == (dims[axis] if side else 0)
+        for al in range(3):
+            if (bnd[f] == 1) == (al == axis):  # 6a: the normal component; 6b: the tangential ones
+                fixed[on, al] = True
+    return fixed.reshape(-1)
 
 
 def validate(problem):
@@ -321,9 +354,15 @@ def validate(problem):
     bad = (mat != PEC) & (mat >= nm)
     if bad.any():
         raise ValueError("material byte outside the table")
-    shell = np.ones_like(mat, dtype=bool)
-    if min(mat.shape) > 2:
-        shell[1:-1, 1:-1, 1:-1] = False
+    bnd = boundary_kinds(problem)
+    shell = np.zeros_like(mat, dtype=bool)  # elements on an absorbing face
+    for f in range(6):
+        if bnd[f] != 0:
+            continue
+        axis, side = f // 2, f % 2  # mat is indexed [k, j, i]
+        idx = [slice(None)] * 3
+        idx[2 - axis] = -1 if side else 0
+        shell[tuple(idx)] = True
     sm = mat[shell]
     if np.any(sm == PEC):
         raise ValueError("PEC touches the outer box")
@@ -394,6 +433,11 @@ def assemble(problem, variant="S", sigma=1.0, s=1.0, maps=None, chunk=20000):
     if variant == "P":
         total = (0.5 * (total + total.T)).tocsr()
         total.sum_duplicates()
+    if maps.fixed.any():
+        # unknowns held at zero (symmetry planes): identity rows and columns
+        keep = sp.diags((~maps.fixed).astype(float))
+        total = (keep @ total @ keep + sp.diags(maps.fixed.astype(float))).tocsr()
+        total.sum_duplicates()
     return total
 
 
@@ -424,6 +468,7 @@ def rhs(problem, waves, sigma=1.0, maps=None):
         corners = element_corner(problem, elems)
         contrib = face_rhs(h, f, corners, k0, waves.k_hat, waves.p_hat, waves.amplitude, sigma)
         np.add.at(B, dofs.ravel(), contrib.reshape(-1, waves.count))
+    B[maps.fixed] = 0.0
     return B
 
 

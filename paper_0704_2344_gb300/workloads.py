@@ -43,6 +43,10 @@ class VoxelProblem:
     mu_r: np.ndarray  # complex128 [n_materials]
     freq_hz: float
     name: str = ""
+    # kind of each box face (-x, +x, -y, +y, -z, +z): 0 absorbing boundary
+    # (Eq. 3), 1 symmetry plane (n . H = 0, Eq. 6a), 2 antisymmetry plane
+    # (n x H = 0, Eq. 6b)
+    boundary: tuple = (0, 0, 0, 0, 0, 0)
 
     @property
     def n_elements(self) -> int:
@@ -271,6 +275,37 @@ def config5(n_requests: int = 512, mean_interarrival_s: float = 0.0,
             t += float(rng.exponential(mean_interarrival_s))
         out.append(Request(t, prob, waves))
     return out
+
+
+def mirror_part(prob: VoxelProblem, x_kind: int = 0, y_kind: int = 0) -> VoxelProblem:
+    """The +x half (x_kind != 0) and/or +y half (y_kind != 0) of a problem
+    that is mirror-symmetric about its mid planes, with those planes turned
+    into symmetry (1) or antisymmetry (2) faces.  The element counts along the
+    cut axes must be even, so that each plane passes through grid nodes."""
+    mat = np.asarray(prob.material)
+    nx, ny = prob.nx, prob.ny
+    x0 = nx // 2 if x_kind else 0
+    y0 = ny // 2 if y_kind else 0
+    if (x_kind and nx % 2) or (y_kind and ny % 2):
+        raise ValueError("the cut axes need an even element count")
+    bnd = list(prob.boundary)
+    if x_kind:
+        bnd[0] = x_kind
+    if y_kind:
+        bnd[2] = y_kind
+    origin = (prob.origin[0] + x0 * prob.h[0], prob.origin[1] + y0 * prob.h[1], prob.origin[2])
+    return VoxelProblem(nx - x0, ny - y0, prob.nz, prob.h, origin,
+                        np.ascontiguousarray(mat[:, y0:, x0:]), prob.eps_r, prob.mu_r, prob.freq_hz,
+                        name=f"{prob.name}_part", boundary=tuple(bnd))
+
+
+def config2_quarter() -> tuple[VoxelProblem, PlaneWaves]:
+    """The +x, +y quarter of the 3-wavelength cube: with H along x at normal
+    incidence the x = mid plane is an antisymmetry plane (n x H = 0) and the
+    y = mid plane a symmetry plane (n . H = 0); the centred PEC cube and the
+    centred slab keep the problem mirror-symmetric about both."""
+    prob, waves = config2()
+    return mirror_part(prob, x_kind=2, y_kind=1), waves
 
 
 def random_small_grid(seed: int, n_max: int = 6, n_pec_boxes: int = 2,
