@@ -40,7 +40,7 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-WORKLOADS = ("config2", "config1", "config3", "config4", "config5")
+WORKLOADS = ("config2", "config1", "config3", "config4", "config5", "config2q")
 
 
 def parse():
@@ -69,7 +69,8 @@ def parse():
 
 def workload(name):
     from paper_0704_2344_gb300 import workloads as W
-    return {"config1": W.config1, "config2": W.config2, "config3": W.config3, "config4": W.config4}[name]()
+    return {"config1": W.config1, "config2": W.config2, "config3": W.config3, "config4": W.config4,
+            "config2q": W.config2_quarter}[name]()
 
 
 class ClockSampler:

@@ -111,6 +111,17 @@ fe_status fe_ctx_synchronize(fe_ctx* ctx);
  * structure of the global matrix).  Built on the device by the library's
  * kernels; the caller's description is copied.
  * ---------------------------------------------------------------------- */
+/* Kind of a box face (Section 3.1.3).  A symmetry or antisymmetry plane
+ * replaces the absorbing condition on that face and lets the box hold one half
+ * (or quarter, eighth) of a mirror-symmetric problem: the face carries no
+ * surface term, may cut through the scatterer, and the held components at its
+ * nodes are fixed at zero (identity rows, zero right-hand side). */
+typedef enum fe_boundary {
+    FE_BOUNDARY_ABC = 0,          /* second-order absorbing condition (Eq. 3); the face's elements must be vacuum */
+    FE_BOUNDARY_SYMMETRY = 1,     /* symmetry plane: n . H = 0 (Eq. 6a), the normal component is held */
+    FE_BOUNDARY_ANTISYMMETRY = 2  /* antisymmetry plane: n x H = 0 (Eq. 6b), the tangential components are held */
+} fe_boundary;
+
 typedef struct fe_mesh_desc {
     int32_t nx, ny, nz;          /* elements per axis, each >= 1 */
     double h[3];                 /* element edge lengths (m), > 0 */
@@ -120,6 +131,7 @@ typedef struct fe_mesh_desc {
     int32_t n_materials;         /* 1..255 entries in eps_r / mu_r */
     const fe_complex* eps_r;     /* host, n_materials relative permittivities (eps' - j eps'' for losses) */
     const fe_complex* mu_r;      /* host, n_materials relative permeabilities */
+    int32_t boundary[6];         /* fe_boundary of the faces -x, +x, -y, +y, -z, +z (all zero: absorbing box) */
 } fe_mesh_desc;
 
 typedef struct fe_mesh_stats {
@@ -133,8 +145,9 @@ typedef struct fe_mesh_stats {
 
 /* Validates the description and builds every integer map on the device.
  * Errors: FE_ERR_INVALID_ARG (sizes, NULL pointers, material byte outside
- * the table), FE_ERR_MESH (PEC or non-vacuum material in the outer layer of
- * elements, i.e. an outer face not in free space), FE_ERR_OOM, FE_ERR_CUDA. */
+ * the table, boundary kind outside 0..2), FE_ERR_MESH (PEC or non-vacuum
+ * material in the outer layer of elements of an absorbing face, i.e. an
+ * absorbing face not in free space), FE_ERR_OOM, FE_ERR_CUDA. */
 fe_status fe_mesh_create(fe_ctx* ctx, const fe_mesh_desc* d, fe_mesh** out);
 fe_status fe_mesh_info(const fe_mesh* m, fe_mesh_stats* out);
 /* Copies the integer maps to caller-allocated HOST buffers; any pointer may

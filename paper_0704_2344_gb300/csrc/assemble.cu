@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                                                   float2* __restrict__ val32, float4* __restrict__ valdf,
                                                   double2* __restrict__ dinv64, float2* __restrict__ dinv32,
                                                   float4* __restrict__ dinvdf, int n_act, int64_t stride,
-                                                  int* __restrict__ status) {
+                                                  unsigned abc, unsigned planes, int* __restrict__ status) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_act) return;
@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
             const bool on_box = side ? ec[axis] == dim[axis] - 1 : ec[axis] == 0;
             int tsel = -1;
             if (on_box) {
-                tsel = n_mat + f;
+                if ((abc >> f) & 1u) tsel = n_mat + f;  // symmetry-plane faces carry no surface term
             } else {
                 int nb[3] = {ei, ej, ek};
                 nb[axis] += side ? 1 : -1;
@@ -218,6 +218,17 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                     acc[q].y += v.y;
                 }
             }
+        }
+    }
+    // unknowns held at zero by symmetry planes: identity rows and columns
+    const unsigned rfix = fixed_components(i, j, k, nx, ny, nz, planes);
+    const unsigned cfix = fixed_components(i + dx, j + dy, k + dz, nx, ny, nz, planes);
+    if (rfix | cfix) {
+#pragma unroll
+        for (int q = 0; q < 9; ++q) {
+            const int al = q / 3, be = q % 3;
+            if (((rfix >> al) & 1u) || ((cfix >> be) & 1u))
+                acc[q] = make_double2(lane == 13 && al == be ? 1.0 : 0.0, 0.0);
         }
     }
 #pragma unroll
@@ -473,7 +484,7 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
                                            (const double2*)s->tables.ptr, (double2*)s->val64.ptr,
                                            (float2*)s->val32.ptr, (float4*)s->valdf.ptr, (double2*)s->dinv64.ptr,
                                            (float2*)s->dinv32.ptr, (float4*)s->dinvdf.ptr, m->n_act, s->stride,
-                                           d_status);
+                                           abc_faces(m->boundary), pack_planes(m->boundary), d_status);
     {
         count_launches(1);
         cudaError_t ce = cudaGetLastError();

@@ -56,6 +56,35 @@ struct DevBuf {
 fe_status dev_alloc(cudaStream_t st, DevBuf& b, size_t bytes);
 void dev_free(cudaStream_t st, DevBuf& b);
 
+// Box faces -x, +x, -y, +y, -z, +z: kinds packed 2 bits per face, and the
+// mask of absorbing faces.
+inline unsigned pack_planes(const int* b) {
+    unsigned p = 0;
+    for (int f = 0; f < 6; ++f) p |= (unsigned)(b[f] & 3) << (2 * f);
+    return p;
+}
+inline unsigned abc_faces(const int* b) {
+    unsigned m = 0;
+    for (int f = 0; f < 6; ++f) m |= (b[f] == FE_BOUNDARY_ABC ? 1u : 0u) << f;
+    return m;
+}
+
+// Bit c set when component c of grid node (i, j, k) is held at zero by a
+// plane face: the normal component on a symmetry plane (Eq. 6a), the two
+// tangential ones on an antisymmetry plane (Eq. 6b).
+__host__ __device__ inline unsigned fixed_components(int i, int j, int k, int nx, int ny, int nz, unsigned planes) {
+    unsigned m = 0;
+    const int c[3] = {i, j, k}, d[3] = {nx, ny, nz};
+    for (int f = 0; f < 6; ++f) {
+        const unsigned kind = (planes >> (2 * f)) & 3u;
+        if (!kind) continue;
+        const int axis = f >> 1;
+        if (c[axis] != ((f & 1) ? d[axis] : 0)) continue;
+        m |= kind == 1u ? (1u << axis) : (7u & ~(1u << axis));
+    }
+    return m;
+}
+
 // Exclusive prefix sum of n int32 values (in may alias out); writes the total
 // to *d_total (device).  Uses `tmp` (grown as needed) for block sums.
 fe_status scan_exclusive(cudaStream_t st, const int* in, int* out, int64_t n, int* d_total, DevBuf& tmp);
@@ -82,6 +111,7 @@ struct fe_mesh {
     int64_t n_el = 0, n_nodes_total = 0;
     int n_act = 0, nnzb = 0, n_ext = 0, n_pec = 0, n_act_el = 0;
     int n_mat = 0;
+    int boundary[6] = {0, 0, 0, 0, 0, 0};  // fe_boundary per face
     std::vector<fe_complex> eps, mu;
     fe::DevBuf material, node_rank, node_id, row_ptr, col_idx, elem_slot, faces_ext, faces_pec;
     int64_t bytes = 0;

@@ -60,7 +60,7 @@ __device__ __forceinline__ unsigned row_mask(unsigned emask) {
 }
 
 __global__ void k_validate(const uint8_t* __restrict__ mat, Grid g, int n_mat, uint32_t vac0, uint32_t vac1,
-                           uint32_t vac2, uint32_t vac3, int* flags) {
+                           uint32_t vac2, uint32_t vac3, unsigned abc, int* flags) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const bool inside = e < (int64_t)g.nx * g.ny * g.nz;
     const unsigned act = __ballot_sync(0xffffffffu, inside && mat[inside ? e : 0] != kPEC);
@@ -69,7 +69,9 @@ __global__ void k_validate(const uint8_t* __restrict__ mat, Grid g, int n_mat, u
     const int i = (int)(e % g.nx), j = (int)((e / g.nx) % g.ny), k = (int)(e / ((int64_t)g.nx * g.ny));
     const unsigned m = mat[e];
     if (m != kPEC && (int)m >= n_mat) atomicOr(&flags[0], 1);
-    const bool shell = i == 0 || j == 0 || k == 0 || i == g.nx - 1 || j == g.ny - 1 || k == g.nz - 1;
+    // elements on an absorbing face (symmetry-plane faces have no vacuum rule)
+    const bool shell = (i == 0 && (abc & 1u)) || (i == g.nx - 1 && (abc & 2u)) || (j == 0 && (abc & 4u)) ||
+                       (j == g.ny - 1 && (abc & 8u)) || (k == 0 && (abc & 16u)) || (k == g.nz - 1 && (abc & 32u));
     if (shell) {
         if (m == kPEC) {
             atomicOr(&flags[0], 2);
@@ -161,7 +163,7 @@ __global__ void k_elem_slot(const uint8_t* __restrict__ mat, Grid g, const int* 
 
 // Outer (Sext) face: a face of an active element on the outer box.  PEC face:
 // a face of an active element whose neighbour across it is PEC.
-__global__ void k_face_flags(const uint8_t* __restrict__ mat, Grid g, int* __restrict__ fext,
+__global__ void k_face_flags(const uint8_t* __restrict__ mat, Grid g, unsigned abc, int* __restrict__ fext,
                              int* __restrict__ fpec, int64_t n_el) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n_el * 6) return;
@@ -172,7 +174,7 @@ __global__ void k_face_flags(const uint8_t* __restrict__ mat, Grid g, int* __res
     const int dim[3] = {g.nx, g.ny, g.nz};
     const bool active = mat[e] != kPEC;
     const bool on_box = side == 0 ? c[axis] == 0 : c[axis] == dim[axis] - 1;
-    int isext = active && on_box;
+    int isext = active && on_box && ((abc >> f) & 1u);  // plane faces are not Sext
     int ispec = 0;
     if (active && !on_box) {
         int n[3] = {c[0], c[1], c[2]};
@@ -206,7 +208,7 @@ static fe_status build(fe_ctx* ctx, fe_mesh* m) {
             vac[q >> 5] |= 1u << (q & 31);
     FE_CUDA(cudaMemsetAsync(d_small, 0, 16 * sizeof(int), st));
     k_validate<<<blocks_for(ne, 256), 256, 0, st>>>((const uint8_t*)m->material.ptr, g, m->n_mat, vac[0], vac[1],
-                                                    vac[2], vac[3], d_small);
+                                                    vac[2], vac[3], abc_faces(m->boundary), d_small);
     FE_LAUNCHED();
 
     // Active nodes and ranks.
@@ -256,8 +258,8 @@ static fe_status build(fe_ctx* ctx, fe_mesh* m) {
     DevBuf fpec_flags, pos;
     FE_TRY(dev_alloc(st, fpec_flags, (size_t)(6 * ne) * sizeof(int)));
     FE_TRY(dev_alloc(st, pos, (size_t)(6 * ne) * sizeof(int)));
-    k_face_flags<<<blocks_for(6 * ne, 256), 256, 0, st>>>((const uint8_t*)m->material.ptr, g, fext,
-                                                          (int*)fpec_flags.ptr, ne);
+    k_face_flags<<<blocks_for(6 * ne, 256), 256, 0, st>>>((const uint8_t*)m->material.ptr, g,
+                                                          abc_faces(m->boundary), fext, (int*)fpec_flags.ptr, ne);
     FE_LAUNCHED();
     FE_TRY(scan_exclusive(st, fext, (int*)pos.ptr, 6 * ne, d_small + 3, ctx->scan_tmp));
     FE_CUDA(cudaMemcpyAsync(h_small + 2, d_small + 2, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -330,6 +332,11 @@ fe_status fe_mesh_create(fe_ctx* ctx, const fe_mesh_desc* d, fe_mesh** out) {
         set_error("fe_mesh_create: grid too large (at most 2^24 elements)");
         return FE_ERR_INVALID_ARG;
     }
+    for (int f = 0; f < 6; ++f)
+        if (d->boundary[f] < FE_BOUNDARY_ABC || d->boundary[f] > FE_BOUNDARY_ANTISYMMETRY) {
+            set_error("fe_mesh_create: boundary[%d] = %d is not a face kind (0..2)", f, d->boundary[f]);
+            return FE_ERR_INVALID_ARG;
+        }
     for (int q = 0; q < d->n_materials; ++q) {
         if (d->eps_r[q].re == 0.0 && d->eps_r[q].im == 0.0) {
             set_error("fe_mesh_create: eps_r[%d] is zero", q);
@@ -353,6 +360,7 @@ fe_status fe_mesh_create(fe_ctx* ctx, const fe_mesh_desc* d, fe_mesh** out) {
     m->n_el = ne;
     m->n_nodes_total = nn;
     m->n_mat = d->n_materials;
+    for (int f = 0; f < 6; ++f) m->boundary[f] = d->boundary[f];
     m->eps.assign(d->eps_r, d->eps_r + d->n_materials);
     m->mu.assign(d->mu_r, d->mu_r + d->n_materials);
     fe_status s = dev_alloc(ctx->stream, m->material, (size_t)ne);

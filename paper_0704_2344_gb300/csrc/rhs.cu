@@ -16,7 +16,8 @@ struct Wave {
 
 __global__ void k_rhs(int nx, int ny, int nz, double hx, double hy, double hz, double ox, double oy, double oz,
                       double k0, double sigma, const int* __restrict__ node_id, int n_act,
-                      const Wave* __restrict__ waves, int nrhs, double2* __restrict__ B) {
+                      const Wave* __restrict__ waves, int nrhs, unsigned abc, unsigned planes,
+                      double2* __restrict__ B) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n_act * nrhs) return;
     const int r = (int)(t / nrhs), w = (int)(t - (int64_t)r * nrhs);
@@ -30,7 +31,7 @@ __global__ void k_rhs(int nx, int ny, int nz, double hx, double hy, double hz, d
     const double g0 = 0.5 - 0.5 / sqrt(3.0), g1 = 0.5 + 0.5 / sqrt(3.0);
     for (int f = 0; f < 6; ++f) {
         const int nu = f >> 1, side = f & 1;
-        if (c[nu] != (side ? dim[nu] : 0)) continue;
+        if (c[nu] != (side ? dim[nu] : 0) || !((abc >> f) & 1u)) continue;  // absorbing faces only
         const int t1 = nu == 0 ? 1 : 0, t2 = nu == 2 ? 1 : 2;
         const double nsgn = side ? 1.0 : -1.0;
         // n . k_hat and the element coordinate along the normal
@@ -84,7 +85,9 @@ __global__ void k_rhs(int nx, int ny, int nz, double hx, double hy, double hz, d
             }
         }
     }
-    for (int al = 0; al < 3; ++al) B[((int64_t)3 * r + al) * nrhs + w] = make_double2(br[al], bi[al]);
+    const unsigned fix = fixed_components(c[0], c[1], c[2], nx, ny, nz, planes);  // held by symmetry planes
+    for (int al = 0; al < 3; ++al)
+        B[((int64_t)3 * r + al) * nrhs + w] = (fix >> al) & 1u ? make_double2(0.0, 0.0) : make_double2(br[al], bi[al]);
 }
 
 fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewave* waves, double2* d_B,
@@ -106,7 +109,8 @@ fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewav
     k_rhs<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(m->nx, m->ny, m->nz, m->h[0], m->h[1], m->h[2],
                                                        m->origin[0], m->origin[1], m->origin[2], s->k0, s->sigma,
                                                        (const int*)m->node_id.ptr, m->n_act,
-                                                       (const Wave*)wave_buf.ptr, nrhs, d_B);
+                                                       (const Wave*)wave_buf.ptr, nrhs, abc_faces(m->boundary),
+                                                       pack_planes(m->boundary), d_B);
     FE_LAUNCHED();
     // the host staging vector must outlive the copy
     FE_CUDA(cudaStreamSynchronize(st));

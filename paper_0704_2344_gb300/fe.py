@@ -25,6 +25,7 @@ FE_ERR_UNSUPPORTED = -8
 
 FE_VARIANT_S, FE_VARIANT_L, FE_VARIANT_P = 0, 1, 2
 FE_PREC_FP64, FE_PREC_MIXED, FE_PREC_DF = 0, 1, 2
+FE_BOUNDARY_ABC, FE_BOUNDARY_SYMMETRY, FE_BOUNDARY_ANTISYMMETRY = 0, 1, 2
 
 LIB_PATH = Path(__file__).resolve().parent / "libfe_gb300.so"
 
@@ -47,7 +48,8 @@ class fe_options(C.Structure):
 class fe_mesh_desc(C.Structure):
     _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double * 3),
                 ("origin", C.c_double * 3), ("material", C.c_void_p), ("material_on_device", C.c_int32),
-                ("n_materials", C.c_int32), ("eps_r", C.POINTER(fe_complex)), ("mu_r", C.POINTER(fe_complex))]
+                ("n_materials", C.c_int32), ("eps_r", C.POINTER(fe_complex)), ("mu_r", C.POINTER(fe_complex)),
+                ("boundary", C.c_int32 * 6)]
 
 
 class fe_mesh_stats(C.Structure):
@@ -219,10 +221,12 @@ def fe_ctx_synchronize(ctx):
     _check(load().fe_ctx_synchronize(ctx), "fe_ctx_synchronize")
 
 
-def fe_mesh_create(ctx, nx, ny, nz, h, origin, material, eps_r, mu_r, material_on_device=False):
-    """material: numpy uint8 array (nz, ny, nx) or a device address of nx*ny*nz bytes."""
+def fe_mesh_create(ctx, nx, ny, nz, h, origin, material, eps_r, mu_r, material_on_device=False, boundary=None):
+    """material: numpy uint8 array (nz, ny, nx) or a device address of nx*ny*nz bytes.
+    boundary: fe_boundary per face (-x, +x, -y, +y, -z, +z); None = absorbing box."""
     lib = load()
     d = fe_mesh_desc()
+    d.boundary = (C.c_int32 * 6)(*[int(v) for v in (boundary or (0,) * 6)])
     d.nx, d.ny, d.nz = int(nx), int(ny), int(nz)
     d.h = (C.c_double * 3)(*[float(v) for v in h])
     d.origin = (C.c_double * 3)(*[float(v) for v in origin])
@@ -253,7 +257,8 @@ def fe_mesh_create_from(ctx, problem, material_device_ptr: int | None = None):
     """Marshals a workloads.VoxelProblem (or any object with the same fields)."""
     mat = problem.material if material_device_ptr is None else material_device_ptr
     return fe_mesh_create(ctx, problem.nx, problem.ny, problem.nz, problem.h, problem.origin, mat,
-                          problem.eps_r, problem.mu_r, material_on_device=material_device_ptr is not None)
+                          problem.eps_r, problem.mu_r, material_on_device=material_device_ptr is not None,
+                          boundary=tuple(getattr(problem, "boundary", (0,) * 6)))
 
 
 def fe_mesh_info(mesh) -> dict:
@@ -452,6 +457,7 @@ def fe_serve_submit(server, problem, waves) -> int:
     d.n_materials = eps.size
     d.eps_r = eps.ctypes.data_as(C.POINTER(fe_complex))
     d.mu_r = mu.ctypes.data_as(C.POINTER(fe_complex))
+    d.boundary = (C.c_int32 * 6)(*[int(v) for v in getattr(problem, "boundary", (0,) * 6)])
     arr = planewave_array(waves)
     r = fe_request()
     r.mesh = d
