@@ -354,6 +354,8 @@ def validate(problem):
     bad = (mat != PEC) & (mat >= nm)
     if bad.any():
         raise ValueError("material byte outside the table")
+    if np.all(mat == PEC):
+        raise ValueError("no active element")
     bnd = boundary_kinds(problem)
     shell = np.zeros_like(mat, dtype=bool)  # elements on an absorbing face
     for f in range(6):

@@ -81,3 +81,11 @@ def test_plane_faces_carry_no_surface_terms_and_may_cut_the_scatterer():
     bad.boundary = (0,) * 6       # the same cut as an absorbing face: PEC on the outer box
     with pytest.raises(ValueError):
         fem.validate(bad)
+
+
+def test_a_mesh_without_active_elements_is_rejected():
+    prob = W.empty_box(3, name="all_pec")
+    prob.material[:] = PEC
+    prob.boundary = (1, 1, 2, 2, 1, 1)
+    with pytest.raises(ValueError):
+        fem.validate(prob)
