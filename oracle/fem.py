@@ -387,12 +387,57 @@ def _coo_add(rows, cols, vals, dofs, mat_block):
     vals.append(np.broadcast_to(mat_block.ravel(), (n, 576)).ravel())
 
 
-def assemble(problem, variant="S", sigma=1.0, s=1.0, maps=None, chunk=20000):
+def pec_surface_dofs(problem, maps):
+    """E formulation: unknowns held at zero on PEC surfaces (n x E = 0).  Around
+    an active node, axis a is a surface normal when two elements of the box
+    that differ only along a are one PEC and one active; every component but
+    a is then tangential and held (at PEC edges and corners all three)."""
+    nx, ny, nz = problem.nx, problem.ny, problem.nz
+    mat = np.asarray(problem.material).reshape(nz, ny, nx)
+    ids = np.flatnonzero(maps.node_active)
+    i = ids % (nx + 1)
+    j = (ids // (nx + 1)) % (ny + 1)
+    k = ids // ((nx + 1) * (ny + 1))
+    pec = np.zeros((ids.size, 8), dtype=bool)
+    act = np.zeros((ids.size, 8), dtype=bool)
+    for b in range(8):
+        ex, ey, ez = b & 1, (b >> 1) & 1, (b >> 2) & 1
+        a, bb, c = i - 1 + ex, j - 1 + ey, k - 1 + ez
+        inside = (a >= 0) & (a < nx) & (bb >= 0) & (bb < ny) & (c >= 0) & (c < nz)
+        m = np.full(ids.size, 0, dtype=np.int64)
+        m[inside] = mat[c[inside], bb[inside], a[inside]]
+        pec[:, b] = inside & (m == PEC)
+        act[:, b] = inside & (m != PEC)
+    held = np.zeros((ids.size, 3), dtype=bool)
+    for axis in range(3):
+        bit = 1 << axis
+        normal = np.zeros(ids.size, dtype=bool)
+        for b in range(8):
+            if b & bit:
+                continue
+            normal |= (pec[:, b] & act[:, b | bit]) | (act[:, b] & pec[:, b | bit])
+        for al in range(3):
+            if al != axis:
+                held[normal, al] = True
+    return held.reshape(-1)
+
+
+def held_dofs(problem, maps, formulation="H"):
+    """All unknowns held at zero: symmetry planes, and PEC surfaces in the E
+    formulation."""
+    if formulation not in ("H", "E"):
+        raise ValueError(formulation)
+    return maps.fixed | pec_surface_dofs(problem, maps) if formulation == "E" else maps.fixed
+
+
+def assemble(problem, variant="S", sigma=1.0, s=1.0, maps=None, chunk=20000, formulation="H"):
     """Global n_dof x n_dof complex128 CSR matrix of Eq. 4's left-hand side.
 
     Element matrices are summed into the global matrix entry by entry
     (coordinate list, duplicates summed); variant 'P' then forms
-    (A_L + A_L^T)/2 (Section 3.1.4)."""
+    (A_L + A_L^T)/2 (Section 3.1.4).  formulation 'E' solves for the total
+    E field with the same steps (Section 2): 1/mu_r in the curl-curl term,
+    eps_r in the mass term, and n x E = 0 held on PEC surfaces."""
     if variant not in ("S", "L", "P"):
         raise ValueError(variant)
     validate(problem)
@@ -415,7 +460,10 @@ def assemble(problem, variant="S", sigma=1.0, s=1.0, maps=None, chunk=20000):
     rows, cols, vals = [], [], []
     act = np.flatnonzero(maps.elem_active)
     for m in np.unique(mflat[act]):
-        ae = element_matrix(h, problem.eps_r[m], problem.mu_r[m], k0, s)
+        if formulation == "E":
+            ae = element_matrix(h, problem.mu_r[m], problem.eps_r[m], k0, s)
+        else:
+            ae = element_matrix(h, problem.eps_r[m], problem.mu_r[m], k0, s)
         el = act[mflat[act] == m]
         for c0 in range(0, el.size, chunk):
             _coo_add(rows, cols, vals, _elem_dofs(maps, el[c0:c0 + chunk]), ae)
@@ -435,10 +483,11 @@ def assemble(problem, variant="S", sigma=1.0, s=1.0, maps=None, chunk=20000):
     if variant == "P":
         total = (0.5 * (total + total.T)).tocsr()
         total.sum_duplicates()
-    if maps.fixed.any():
-        # unknowns held at zero (symmetry planes): identity rows and columns
-        keep = sp.diags((~maps.fixed).astype(float))
-        total = (keep @ total @ keep + sp.diags(maps.fixed.astype(float))).tocsr()
+    held = held_dofs(problem, maps, formulation)
+    if held.any():
+        # unknowns held at zero (symmetry planes, PEC surfaces for E): identity rows and columns
+        keep = sp.diags((~held).astype(float))
+        total = (keep @ total @ keep + sp.diags(held.astype(float))).tocsr()
         total.sum_duplicates()
     return total
 
@@ -455,9 +504,10 @@ def element_corner(problem, e):
     return o + np.stack([i, j, k], axis=-1).astype(float) * h
 
 
-def rhs(problem, waves, sigma=1.0, maps=None):
+def rhs(problem, waves, sigma=1.0, maps=None, formulation="H"):
     """B[n_dof, R]: right-hand side of Eq. 4 for each plane wave, summed over
-    the outer (Sext) faces."""
+    the outer (Sext) faces (the waves' p_hat polarises the formulation's
+    field, H or E)."""
     maps = maps if maps is not None else mesh_maps(problem)
     k0 = wavenumber(problem.freq_hz)
     h = tuple(float(v) for v in problem.h)
@@ -470,7 +520,7 @@ def rhs(problem, waves, sigma=1.0, maps=None):
         corners = element_corner(problem, elems)
         contrib = face_rhs(h, f, corners, k0, waves.k_hat, waves.p_hat, waves.amplitude, sigma)
         np.add.at(B, dofs.ravel(), contrib.reshape(-1, waves.count))
-    B[maps.fixed] = 0.0
+    B[held_dofs(problem, maps, formulation)] = 0.0
     return B
 
 
