@@ -83,11 +83,24 @@ typedef enum fe_precision {
                           the FP32 pipes), everything else FP64; converges like FE_PREC_FP64 */
 } fe_precision;
 
+/* The field solved for (Section 2: every step of the H formulation applies
+ * to E as well).  FE_FORMULATION_E puts 1/mu_r in the curl-curl term and
+ * eps_r in the mass term, and holds n x E = 0 on conductor surfaces
+ * (Section 3.1.3): the tangential E components at nodes on PEC surfaces are
+ * fixed at zero (at PEC edges and corners all three).  Plane waves then give
+ * the incident E (p_hat its polarisation), the solution is the total E, and
+ * the symmetry-plane kinds refer to E. */
+typedef enum fe_formulation {
+    FE_FORMULATION_H = 0,
+    FE_FORMULATION_E = 1
+} fe_formulation;
+
 typedef struct fe_options {
     void* stream;      /* cudaStream_t for all work of the context; NULL = context-owned stream */
     int32_t variant;   /* fe_variant; default FE_VARIANT_S */
     double abc_sigma;  /* weight of the transverse ABC term: +1 Eq. 3 as printed (default, absorbing for every mode), -1 Taylor sign, 0 first order */
     double penalty_s;  /* grad-div penalty coefficient s (Eq. 2); default 1 */
+    int32_t formulation; /* fe_formulation; default FE_FORMULATION_H */
 } fe_options;
 
 /* Fills *opt with the defaults above. */

@@ -144,6 +144,7 @@ void fe_options_default(fe_options* opt) {
     opt->variant = FE_VARIANT_S;
     opt->abc_sigma = 1.0;
     opt->penalty_s = 1.0;
+    opt->formulation = FE_FORMULATION_H;
 }
 
 const char* fe_last_error(void) { return g_err; }
@@ -161,6 +162,10 @@ fe_status fe_ctx_create(fe_ctx** out, int cuda_device, const fe_options* opt) {
     if (opt) o = *opt;
     if (o.variant < FE_VARIANT_S || o.variant > FE_VARIANT_P) {
         set_error("fe_ctx_create: unknown variant %d", o.variant);
+        return FE_ERR_INVALID_ARG;
+    }
+    if (o.formulation != FE_FORMULATION_H && o.formulation != FE_FORMULATION_E) {
+        set_error("fe_ctx_create: unknown formulation %d", o.formulation);
         return FE_ERR_INVALID_ARG;
     }
     int ndev = 0;

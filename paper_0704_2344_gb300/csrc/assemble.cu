@@ -148,7 +148,8 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
                                                   float2* __restrict__ val32, float4* __restrict__ valdf,
                                                   double2* __restrict__ dinv64, float2* __restrict__ dinv32,
                                                   float4* __restrict__ dinvdf, int n_act, int64_t stride,
-                                                  unsigned abc, unsigned planes, int* __restrict__ status) {
+                                                  unsigned abc, unsigned planes, int form_e,
+                                                  int* __restrict__ status) {
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (warp >= n_act) return;
@@ -221,8 +222,13 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
         }
     }
     // unknowns held at zero by symmetry planes: identity rows and columns
-    const unsigned rfix = fixed_components(i, j, k, nx, ny, nz, planes);
-    const unsigned cfix = fixed_components(i + dx, j + dy, k + dz, nx, ny, nz, planes);
+    // (and, for E, the tangential components on conductor surfaces)
+    unsigned rfix = fixed_components(i, j, k, nx, ny, nz, planes);
+    unsigned cfix = fixed_components(i + dx, j + dy, k + dz, nx, ny, nz, planes);
+    if (form_e) {
+        rfix |= pec_held(mat, nx, ny, nz, i, j, k);
+        cfix |= pec_held(mat, nx, ny, nz, i + dx, j + dy, k + dz);
+    }
     if (rfix | cfix) {
 #pragma unroll
         for (int q = 0; q < 9; ++q) {
@@ -280,7 +286,7 @@ __global__ void __launch_bounds__(256) k_assemble(const uint8_t* __restrict__ ma
 // 8 elements around it are active, of one material, and have no outer face
 // and no PEC neighbour (so no face term reaches the row in any variant).
 __global__ void k_row_class(const uint8_t* __restrict__ mat, int nx, int ny, int nz, const int* __restrict__ node_id,
-                            int n_act, signed char* __restrict__ cls, int* __restrict__ rep) {
+                            int n_act, int form_e, signed char* __restrict__ cls, int* __restrict__ rep) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r >= n_act) return;
     const int id = node_id[r];
@@ -300,6 +306,12 @@ __global__ void k_row_class(const uint8_t* __restrict__ mat, int nx, int ny, int
                     for (int f = 0; f < 6 && ok; ++f)
                         if (mat[nb[f][0] + (int64_t)nx * (nb[f][1] + (int64_t)ny * nb[f][2])] == kPEC) ok = false;
                 }
+        // E: no neighbour on a conductor surface either (its held columns would
+        // differ from the class stencil): no PEC in the 4 x 4 x 4 elements around
+        for (int ez = -2; ez < 2 && ok && form_e; ++ez)
+            for (int ey = -2; ey < 2 && ok; ++ey)
+                for (int ex = -2; ex < 2 && ok; ++ex)
+                    if (mat[(i + ex) + (int64_t)nx * ((j + ey) + (int64_t)ny * (k + ez))] == kPEC) ok = false;
         if (ok) c = m;
     }
     cls[r] = (signed char)c;
@@ -433,6 +445,7 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
     s->k0 = 2.0 * kPi * freq_hz / kC0;
     s->precision = precision;
     s->variant = ctx->opt.variant;
+    s->formulation = ctx->opt.formulation;
     s->sigma = ctx->opt.abc_sigma;
     s->s_pen = ctx->opt.penalty_s;
     cudaStream_t st = ctx->stream;
@@ -463,8 +476,11 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
     P.variant = s->variant;
     P.n_mat = m->n_mat;
     for (int q = 0; q < m->n_mat; ++q) {
-        P.eps[q] = Cx{m->eps[q].re, m->eps[q].im};
-        P.mu[q] = Cx{m->mu[q].re, m->mu[q].im};
+        // the E formulation is the H formulation with the material roles exchanged
+        const fe_complex& ce = s->formulation == FE_FORMULATION_E ? m->mu[q] : m->eps[q];
+        const fe_complex& cm = s->formulation == FE_FORMULATION_E ? m->eps[q] : m->mu[q];
+        P.eps[q] = Cx{ce.re, ce.im};
+        P.mu[q] = Cx{cm.re, cm.im};
     }
     int* d_status = (int*)ctx->small.ptr + 8;
     cudaMemsetAsync(d_status, 0, sizeof(int), st);
@@ -484,7 +500,8 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
                                            (const double2*)s->tables.ptr, (double2*)s->val64.ptr,
                                            (float2*)s->val32.ptr, (float4*)s->valdf.ptr, (double2*)s->dinv64.ptr,
                                            (float2*)s->dinv32.ptr, (float4*)s->dinvdf.ptr, m->n_act, s->stride,
-                                           abc_faces(m->boundary), pack_planes(m->boundary), d_status);
+                                           abc_faces(m->boundary), pack_planes(m->boundary),
+                                           s->formulation == FE_FORMULATION_E ? 1 : 0, d_status);
     {
         count_launches(1);
         cudaError_t ce = cudaGetLastError();
@@ -502,7 +519,7 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         cudaMemcpyAsync(d_rep, big.data(), kMaxClasses * sizeof(int), cudaMemcpyHostToDevice, st);
         k_row_class<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
             (const uint8_t*)m->material.ptr, m->nx, m->ny, m->nz, (const int*)m->node_id.ptr, m->n_act,
-            (signed char*)s->row_class.ptr, d_rep);
+            s->formulation == FE_FORMULATION_E ? 1 : 0, (signed char*)s->row_class.ptr, d_rep);
         count_launches(1);
         k_class_stencil<<<kMaxClasses, 32, 0, st>>>((const double2*)s->val64.ptr, s->stride,
                                                     (const int*)m->row_ptr.ptr, d_rep, (StencilSet*)s->stencil.ptr);

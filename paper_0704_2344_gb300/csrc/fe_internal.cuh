@@ -85,6 +85,34 @@ __host__ __device__ inline unsigned fixed_components(int i, int j, int k, int nx
     return m;
 }
 
+// E formulation: bit c set when component c of grid node (i, j, k) is held at
+// zero on a conductor surface (n x E = 0).  Axis a is a surface normal at
+// the node when two of its (up to) eight elements that differ only along a
+// are one PEC and one active; every component but a is then tangential.
+__device__ inline unsigned pec_held(const uint8_t* __restrict__ mat, int nx, int ny, int nz, int i, int j, int k) {
+    unsigned pec = 0, act = 0;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const int a = i - 1 + (b & 1), c = j - 1 + ((b >> 1) & 1), d = k - 1 + ((b >> 2) & 1);
+        if (a < 0 || a >= nx || c < 0 || c >= ny || d < 0 || d >= nz) continue;
+        if (mat[a + (int64_t)nx * (c + (int64_t)ny * d)] == kPEC) pec |= 1u << b;
+        else act |= 1u << b;
+    }
+    unsigned held = 0;
+#pragma unroll
+    for (int axis = 0; axis < 3; ++axis) {
+        const unsigned bit = 1u << axis;
+        bool normal = false;
+#pragma unroll
+        for (unsigned b = 0; b < 8; ++b)
+            if (!(b & bit) && ((((pec >> b) & 1u) && ((act >> (b | bit)) & 1u)) ||
+                               (((act >> b) & 1u) && ((pec >> (b | bit)) & 1u))))
+                normal = true;
+        if (normal) held |= 7u & ~bit;
+    }
+    return held;
+}
+
 // Exclusive prefix sum of n int32 values (in may alias out); writes the total
 // to *d_total (device).  Uses `tmp` (grown as needed) for block sums.
 fe_status scan_exclusive(cudaStream_t st, const int* in, int* out, int64_t n, int* d_total, DevBuf& tmp);
@@ -123,6 +151,7 @@ struct fe_system {
     double freq = 0, k0 = 0;
     int precision = FE_PREC_MIXED;
     int variant = FE_VARIANT_S;
+    int formulation = FE_FORMULATION_H;
     double sigma = -1, s_pen = 1;
     fe::DevBuf tables;               // double2 [(n_mat + 12) * 576], block-major
     // Block values are stored as 9 planes, one per block entry (alpha, beta):

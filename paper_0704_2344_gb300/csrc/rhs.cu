@@ -17,7 +17,7 @@ struct Wave {
 __global__ void k_rhs(int nx, int ny, int nz, double hx, double hy, double hz, double ox, double oy, double oz,
                       double k0, double sigma, const int* __restrict__ node_id, int n_act,
                       const Wave* __restrict__ waves, int nrhs, unsigned abc, unsigned planes,
-                      double2* __restrict__ B) {
+                      const uint8_t* __restrict__ mat, int form_e, double2* __restrict__ B) {
     const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= (int64_t)n_act * nrhs) return;
     const int r = (int)(t / nrhs), w = (int)(t - (int64_t)r * nrhs);
@@ -85,7 +85,9 @@ __global__ void k_rhs(int nx, int ny, int nz, double hx, double hy, double hz, d
             }
         }
     }
-    const unsigned fix = fixed_components(c[0], c[1], c[2], nx, ny, nz, planes);  // held by symmetry planes
+    // held by symmetry planes (and, for E, on conductor surfaces)
+    unsigned fix = fixed_components(c[0], c[1], c[2], nx, ny, nz, planes);
+    if (form_e) fix |= pec_held(mat, nx, ny, nz, c[0], c[1], c[2]);
     for (int al = 0; al < 3; ++al)
         B[((int64_t)3 * r + al) * nrhs + w] = (fix >> al) & 1u ? make_double2(0.0, 0.0) : make_double2(br[al], bi[al]);
 }
@@ -110,7 +112,8 @@ fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewav
                                                        m->origin[0], m->origin[1], m->origin[2], s->k0, s->sigma,
                                                        (const int*)m->node_id.ptr, m->n_act,
                                                        (const Wave*)wave_buf.ptr, nrhs, abc_faces(m->boundary),
-                                                       pack_planes(m->boundary), d_B);
+                                                       pack_planes(m->boundary), (const uint8_t*)m->material.ptr,
+                                                       s->formulation == FE_FORMULATION_E ? 1 : 0, d_B);
     FE_LAUNCHED();
     // the host staging vector must outlive the copy
     FE_CUDA(cudaStreamSynchronize(st));

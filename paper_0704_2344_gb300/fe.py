@@ -26,6 +26,7 @@ FE_ERR_UNSUPPORTED = -8
 FE_VARIANT_S, FE_VARIANT_L, FE_VARIANT_P = 0, 1, 2
 FE_PREC_FP64, FE_PREC_MIXED, FE_PREC_DF = 0, 1, 2
 FE_BOUNDARY_ABC, FE_BOUNDARY_SYMMETRY, FE_BOUNDARY_ANTISYMMETRY = 0, 1, 2
+FE_FORMULATION_H, FE_FORMULATION_E = 0, 1
 
 LIB_PATH = Path(__file__).resolve().parent / "libfe_gb300.so"
 
@@ -42,7 +43,7 @@ class fe_complex(C.Structure):
 
 class fe_options(C.Structure):
     _fields_ = [("stream", C.c_void_p), ("variant", C.c_int32), ("abc_sigma", C.c_double),
-                ("penalty_s", C.c_double)]
+                ("penalty_s", C.c_double), ("formulation", C.c_int32)]
 
 
 class fe_mesh_desc(C.Structure):
@@ -200,7 +201,7 @@ def _ptr(a) -> int:
 
 # --------------------------------------------------------------------------
 def fe_ctx_create(device: int = 0, stream: int | None = None, variant: int = FE_VARIANT_S,
-                  abc_sigma: float = 1.0, penalty_s: float = 1.0):
+                  abc_sigma: float = 1.0, penalty_s: float = 1.0, formulation: int = 0):
     lib = load()
     opt = fe_options()
     lib.fe_options_default(C.byref(opt))
@@ -208,6 +209,7 @@ def fe_ctx_create(device: int = 0, stream: int | None = None, variant: int = FE_
     opt.variant = variant
     opt.abc_sigma = abc_sigma
     opt.penalty_s = penalty_s
+    opt.formulation = formulation
     out = P()
     _check(lib.fe_ctx_create(C.byref(out), device, C.byref(opt)), "fe_ctx_create")
     return out
