@@ -147,7 +147,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     // class stencils and cost-balanced product ranges pay off for the
     // complex64 and FP32-pair products; the FP64 products stay explicit and
     // uniform
-    const bool classes = !fp64 && !(df && getenv("FE_DF_NOCLASS"));
+    const bool classes = !fp64;
     P.row_class = classes ? (const signed char*)s->row_class.ptr : nullptr;
     P.stencil = (const StencilSet*)s->stencil.ptr;
     P.cost_prefix = classes ? (const int*)(df ? s->cost_prefix_alu.ptr : s->cost_prefix.ptr) : nullptr;
@@ -188,7 +188,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.rep_outer = ri + 2 * R;
     P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
     P.timeout_ns = 1000ull * (unsigned long long)(o.wait_timeout_us > 0 ? o.wait_timeout_us : 4000000);
-    P.spin_ns = getenv("FE_SPIN_NS") ? (unsigned)atoi(getenv("FE_SPIN_NS")) : 0u;
+    P.spin_ns = 0;  // barrier waits poll without back-off (measured fastest)
 }
 
 // Solves tile by tile; b and x are device arrays [n_dof][nrhs].
