@@ -9,7 +9,10 @@
  * PEC surfaces, and the incident plane-wave right-hand side of Eq. 4.
  * Geometry is a voxel box of first-order (trilinear) hexahedra.  Unknowns are
  * the three Cartesian H components at every active node ("three lines per
- * node", Section 3.1.2), stored as a 3x3-block sparse row matrix.
+ * node", Section 3.1.2), stored as a 3x3-block sparse row matrix.  A box face
+ * may instead be a symmetry or antisymmetry plane (Section 3.1.3, Eqs.
+ * 6a/6b), and a context may solve for the total E field instead of H
+ * (Section 2; n x E = 0 held on conductors).
  *
  * Conventions used by every call
  *   - Units SI, time dependence e^{j omega t}, c0 = 299 792 458 m/s,
