@@ -4,4 +4,4 @@ TEST INFRASTRUCTURE ONLY: tests/, __graft_entry__.smoke() and bench.py's
 CPU-baseline / reference legs may import it.  The library itself never
 imports, links or runs anything here, and the two share no code.
 """
-from . import fem, krylov  # noqa: F401
+from . import fem, krylov, precond  # noqa: F401

@@ -9,7 +9,9 @@ Hermitian) matrix the consistent form of CG uses the unconjugated bilinear
 form u^T v everywhere (the paper's incomplete Cholesky likewise squares L
 entries instead of taking moduli, Eq. 5): this is COCG.  The diagonal
 preconditioner is generalised to the 3x3 diagonal blocks of the node rows
-(Section 3.1.2 stores three rows per node).
+(Section 3.1.2 stores three rows per node); any other preconditioner, such as
+the block incomplete Cholesky of Section 3.1.5.3 (oracle/precond.py), can be
+passed in as the callable M.
 
 Each step follows the textbook order: q = A p, alpha = rho / p^T q,
 x += alpha p, r -= alpha q, z = D^{-1} r, rho' = r^T z, p = z + (rho'/rho) p.
@@ -35,20 +37,23 @@ def apply_block(Dinv, r):
     return np.einsum("nab,nb->na", Dinv, r.reshape(-1, 3)).reshape(-1)
 
 
-def cocg(A, b, tol=1e-8, maxiter=100000, x0=None, Dinv=None):
-    """Solve A x = b (A complex symmetric) by block-Jacobi COCG until the
-    recursive residual satisfies ||r||_2 <= tol ||b||_2.  Returns (x, iters,
+def cocg(A, b, tol=1e-8, maxiter=100000, x0=None, Dinv=None, M=None):
+    """Solve A x = b (A complex symmetric) by preconditioned COCG until the
+    recursive residual satisfies ||r||_2 <= tol ||b||_2.  The preconditioner
+    is z = M(r) when M is given, else block Jacobi.  Returns (x, iters,
     history of ||r||/||b||)."""
     b = np.asarray(b, dtype=complex).reshape(-1)
-    if Dinv is None:
-        Dinv = block_jacobi_inverse(A)
+    if M is None:
+        if Dinv is None:
+            Dinv = block_jacobi_inverse(A)
+        M = lambda v: apply_block(Dinv, v)  # noqa: E731
     x = np.zeros_like(b) if x0 is None else np.array(x0, dtype=complex).reshape(-1)
     r = b - A @ x
     nb = np.linalg.norm(b)
     hist = [np.linalg.norm(r) / nb]
     if hist[-1] <= tol:
         return x, 0, hist
-    z = apply_block(Dinv, r)
+    z = M(r)
     p = z.copy()
     rho = r @ z
     it = 0
@@ -61,7 +66,7 @@ def cocg(A, b, tol=1e-8, maxiter=100000, x0=None, Dinv=None):
         hist.append(np.linalg.norm(r) / nb)
         if hist[-1] <= tol:
             break
-        z = apply_block(Dinv, r)
+        z = M(r)
         rho_new = r @ z
         p = z + (rho_new / rho) * p
         rho = rho_new
