@@ -50,7 +50,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="config2", choices=WORKLOADS)
-    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "df"],
+    ap.add_argument("--precision", default="auto", choices=["auto", "mixed", "fp64", "df", "fp64_bicp"],
                     help="auto: time both and report the faster one that reaches the tolerance")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
@@ -232,10 +232,13 @@ def run_ours(args, rank, world, local_rank, precision_name):
     build.build()
     torch.cuda.set_device(local_rank)
     prob, waves = workload(args.workload)
-    precision = {"mixed": fe.FE_PREC_MIXED, "fp64": fe.FE_PREC_FP64, "df": fe.FE_PREC_DF}[precision_name]
+    bicp = precision_name == "fp64_bicp"   # FP64 with the block incomplete Cholesky preconditioner
+    base = "fp64" if bicp else precision_name
+    precision = {"mixed": fe.FE_PREC_MIXED, "fp64": fe.FE_PREC_FP64, "df": fe.FE_PREC_DF}[base]
     stream = torch.cuda.Stream()
     ctx = fe.fe_ctx_create(local_rank, stream=stream.cuda_stream)
-    opts = fe.solve_opts(precision=precision, tol=1e-8, rhs_tile=args.rhs_tile)
+    opts = fe.solve_opts(precision=precision, tol=1e-8, rhs_tile=args.rhs_tile,
+                         preconditioner=fe.FE_PRECOND_BICP if bicp else fe.FE_PRECOND_BLOCK_JACOBI)
     mat_d = torch.from_numpy(np.ascontiguousarray(prob.material).ravel()).to(f"cuda:{local_rank}")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
     R = waves.count
@@ -245,6 +248,8 @@ def run_ours(args, rank, world, local_rank, precision_name):
         try:
             system = fe.fe_assemble(ctx, mesh, prob.freq_hz, precision)
             try:
+                if bicp:
+                    fe.fe_system_factor_bicp(ctx, system, 0)
                 n_dof = fe.fe_mesh_info(mesh)["n_dof"]
                 if device_inputs:
                     st, _, rep = fe.fe_solve_batch(ctx, system, waves, n_dof, opts, x_out=x_dev.data_ptr(),
@@ -263,6 +268,15 @@ def run_ours(args, rank, world, local_rank, precision_name):
     info = fe.fe_mesh_info(mesh0)
     sys0 = fe.fe_assemble(ctx, mesh0, prob.freq_hz, precision)
     sysinfo = fe.fe_system_info(sys0)
+    bicp_blocks = 0
+    if bicp:  # strictly lower blocks inside the bands: the substitutions' work
+        n_band = fe.fe_system_factor_bicp(ctx, sys0, 0)
+        mp = fe.fe_mesh_export_maps(ctx, mesh0)
+        rows = np.repeat(np.arange(info["n_nodes"]), np.diff(mp["row_ptr"]))
+        band = np.searchsorted((np.arange(n_band + 1) * info["n_nodes"]) // n_band, np.arange(info["n_nodes"]),
+                               side="right") - 1
+        cols = mp["col_idx"].astype(np.int64)
+        bicp_blocks = int(np.count_nonzero((cols < rows) & (band[cols] == band[rows])))
     fe.fe_system_destroy(sys0)
     fe.fe_mesh_destroy(mesh0)
     x_dev = torch.empty((info["n_dof"], R), dtype=torch.complex128, device=f"cuda:{local_rank}")
@@ -307,8 +321,14 @@ def run_ours(args, rank, world, local_rank, precision_name):
         e2e_ms.append((time.perf_counter() - t0) * 1e3)
     ms_local = total_ms / args.steps
     ms = replicas.max_over_ranks([ms_local], device=f"cuda:{local_rank}")[0]  # the slowest rank
-    alg, inner_b, outer_b = algorithmic_bytes(info, sysinfo, precision_name, inner_iters / R, passes, R)
-    fl_prod, fl64 = algorithmic_flops(info, sysinfo, precision_name, inner_iters / R, passes, R)
+    alg, inner_b, outer_b = algorithmic_bytes(info, sysinfo, base, inner_iters / R, passes, R)
+    fl_prod, fl64 = algorithmic_flops(info, sysinfo, base, inner_iters / R, passes, R)
+    if bicp:
+        # forward and back substitution per iteration and column: 2 x 9 complex
+        # multiply-adds per band block below the diagonal, 2 x 6 per node (the
+        # triangular L_II^{-1}), instead of block Jacobi's 9 per node
+        fl64 += inner_iters * 8.0 * (18.0 * bicp_blocks + 3.0 * info["n_nodes"])
+        alg += inner_iters / R * (bicp_blocks * 9 * 16.0 * 2 + info["n_nodes"] * 9 * 16.0 * 2)
     launch_ms = kernel_ms / args.steps
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
@@ -319,15 +339,18 @@ def run_ours(args, rank, world, local_rank, precision_name):
     common = {"algorithmic_bytes_per_launch": int(alg / args.steps),
               "product_flops_per_launch": int(fl_prod / args.steps), "fp64_flops_per_launch": int(fl64 / args.steps),
               "product_rows": dict(zip(("blocks_explicit", "rows_general", "rows_diagonal"),
-                                       product_rows(sysinfo, precision_name)))}
-    if precision_name == "fp64":
+                                       product_rows(sysinfo, base)))}
+    if bicp:
+        common["bicp_band_blocks"] = bicp_blocks
+    if base == "fp64":
         # the complex128 products run on the FP64 pipes (1/64 of the FP32 rate on GB300): ALU-bound
         achieved = (fl_prod + fl64) / secs / 1e12 if secs > 0 else None
-        roof = {"kernel": f"k_solve<double,{R}> (persistent COCG, FP64)", "bound": "alu",
+        roof = {"kernel": f"k_solve<double,{R}> (persistent COCG, FP64"
+                          + (", block incomplete Cholesky)" if bicp else ")"), "bound": "alu",
                 "achieved": round(achieved, 4) if achieved else None, "peak": round(FP64_PEAK_TFLOPS, 3),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4) if achieved else None,
                 "peak_source": "FP64 rate from unit counts and clock (1.20 measured)", "hbm_view": hbm_view}
-    elif precision_name == "df":
+    elif base == "df":
         # FP32-pair products on the FP32 pipes; the FP64 vector work issues
         # at 1/64 of that rate, so it is counted as 64 FP32-equivalent flops
         achieved = (fl_prod + 64.0 * fl64) / secs / 1e12 if secs > 0 else None
@@ -359,7 +382,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"mixed": "c64+f64", "fp64": "c128", "df": "f32x2+f64"}[precision_name],
+        "dtype": {"mixed": "c64+f64", "fp64": "c128", "df": "f32x2+f64", "fp64_bicp": "c128"}[precision_name],
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {prob.name}, {info['n_dof']} unknowns, {R} plane wave(s)",
                    "n_dof": info["n_dof"], "nnzb": info["nnzb"], "rhs": R, "precision": precision_name,
@@ -714,7 +737,7 @@ def main():
             import torch
             torch.distributed.destroy_process_group()
         return
-    modes = ["fp64", "mixed", "df"] if args.precision == "auto" else [args.precision]
+    modes = ["fp64", "mixed", "df", "fp64_bicp"] if args.precision == "auto" else [args.precision]
     lines = {m: run_ours(args, rank, world, local_rank, m) for m in modes}
     # headline: the fastest mode that reached 1e-8 on every step
     ok = [m for m in modes if lines[m]["converged"]] or modes

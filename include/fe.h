@@ -210,6 +210,31 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out);
  * (re_hi, im_hi, re_lo, im_lo), block-major as vals_c128.  Errors:
  * FE_ERR_INVALID_ARG (NULL, or the system has no FP32-pair copy). */
 fe_status fe_system_export_df(fe_ctx* ctx, const fe_system* s, void* vals_df);
+
+/* Block incomplete Cholesky preconditioner, BICP (Section 3.1.5.3; the
+ * factor of Section 3.1.5.2, Eq. 5; its application by the forward and back
+ * substitutions of Eq. 6).  The node rows are split into n_sub contiguous
+ * bands, band b holding nodes floor(b n / n_sub) <= I < floor((b+1) n / n_sub)
+ * (n = active nodes); each band gets the incomplete Cholesky factor of its
+ * own diagonal block on the lower 3x3-block pattern of A, unconjugated
+ * (A ~ L L^T, L L^T = A on every stored block of the band), and couplings
+ * between bands are dropped.  The persistent solve runs one CTA per band, so
+ * a solve with fe_solve_opts.preconditioner = FE_PRECOND_BICP needs a factor
+ * with as many bands as its grid: n_sub = 0 picks that number, min(SMs, n).
+ * The factor is FP64 and is used by FE_PREC_FP64 solves.  It is built on the
+ * device (one thread per band) and kept with the system (16 B x 9 per stored
+ * block, plus index arrays); a new call replaces it.
+ * Errors: FE_ERR_INVALID_ARG (NULL, no rows, n_sub outside [0, n]),
+ * FE_ERR_BREAKDOWN (a pivot is zero or not finite; no factor is kept),
+ * FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_system_factor_bicp(fe_ctx* ctx, fe_system* s, int32_t n_sub);
+
+/* Copies the factor to the host: l_c128 (optional) complex128 [nnzb][3][3]
+ * in block-slot order: L_IJ at the slot of block (I, J) for J < I in I's
+ * band, the lower triangular L_II at the diagonal slot, zeros elsewhere;
+ * n_sub (optional) receives the number of bands.  Errors:
+ * FE_ERR_INVALID_ARG (NULL, or no factor), FE_ERR_CUDA. */
+fe_status fe_system_export_bicp(fe_ctx* ctx, const fe_system* s, void* l_c128, int32_t* n_sub);
 void fe_system_destroy(fe_system* s);
 
 /* ------------------------------------------------------------------------
@@ -252,6 +277,13 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
  * rhs_tile right-hand sides are solved together in one persistent device
  * launch.
  * ---------------------------------------------------------------------- */
+typedef enum fe_preconditioner {
+    FE_PRECOND_BLOCK_JACOBI = 0, /* inverse 3x3 node blocks (the diagonal preconditioning of Section
+                                    3.1.5.1 on the node blocks); every precision */
+    FE_PRECOND_BICP = 1          /* block incomplete Cholesky, one band per CTA (fe_system_factor_bicp
+                                    first); FE_PREC_FP64 only, one system per launch */
+} fe_preconditioner;
+
 typedef struct fe_solve_opts {
     int32_t precision;   /* fe_precision; default FE_PREC_DF */
     double tol;          /* true FP64 relative residual target; default 1e-8 */
@@ -267,6 +299,7 @@ typedef struct fe_solve_opts {
     int32_t wait_timeout_us; /* bound on every device-side wait of the solve (grid barriers, copy
                               completions); on expiry the solve ends with FE_ERR_TIMEOUT and the
                               context stays usable; 0 = default 4 000 000 (4 s) */
+    int32_t preconditioner; /* fe_preconditioner; default FE_PRECOND_BLOCK_JACOBI */
 } fe_solve_opts;
 
 void fe_solve_opts_default(fe_solve_opts* o);

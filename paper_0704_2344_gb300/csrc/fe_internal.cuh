@@ -178,6 +178,18 @@ struct fe_system {
     int64_t cost_total_alu = 0;
     int cost_min[2] = {1, 1}, cost_max[2] = {1, 1};  // bounds of one row's cost (complex64, FP32 pairs)
     int64_t rows_general = 0, rows_diagonal = 0, blocks_explicit = 0;  // rows per product path
+    // Block incomplete Cholesky factor (Section 3.1.5.3): node rows split into
+    // bicp_n_sub contiguous bands, floor(b n / S) <= I < floor((b + 1) n / S),
+    // one per CTA of the solve; L L^T reproduces A on the lower node-block
+    // pattern of each band.
+    int bicp_n_sub = 0;
+    fe::DevBuf bicp_l;               // double2 [nnzb * 9]: L_IJ at block slot (I, J), row-major 3x3
+                                     //   (J < I in I's band; L_II lower triangular; zero elsewhere)
+    fe::DevBuf bicp_linv;            // double2 [n_act * 9]: L_II^{-1} (lower triangular)
+    fe::DevBuf bicp_tpos;            // int [nnzb]: slot of block (J, I) for the block (I, J)
+    fe::DevBuf bicp_order;           // int [n_act]: each band's nodes sorted by level, in the band's range
+    fe::DevBuf bicp_lev;             // int [n_act + n_sub]: band b's level offsets at [first node + b, ...]
+    fe::DevBuf bicp_nlev;            // int [n_sub]: levels per band
 };
 
 namespace fe {

@@ -81,6 +81,8 @@ static const void* inner_matrix(const fe_system* s, int prec) {
     return prec == FE_PREC_FP64 ? s->val64.ptr : (prec == FE_PREC_MIXED ? s->val32.ptr : s->valdf.ptr);
 }
 
+static fe_status check_precond(const fe_ctx* ctx, const fe_system* s, const fe_solve_opts& o, const char* what);
+
 static fe_status check_system_precision(const fe_system* s, int prec, const char* who) {
     if (!inner_matrix(s, prec)) {
         set_error("%s: the system was not assembled for precision %d (assemble with that precision)", who, prec);
@@ -189,6 +191,14 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
     P.timeout_ns = 1000ull * (unsigned long long)(o.wait_timeout_us > 0 ? o.wait_timeout_us : 4000000);
     P.spin_ns = 0;  // barrier waits poll without back-off (measured fastest)
+    if (o.preconditioner == FE_PRECOND_BICP && fp64) {
+        P.bicp_l = (const double2*)s->bicp_l.ptr;
+        P.bicp_linv = (const double2*)s->bicp_linv.ptr;
+        P.bicp_tpos = (const int*)s->bicp_tpos.ptr;
+        P.bicp_order = (const int*)s->bicp_order.ptr;
+        P.bicp_lev = (const int*)s->bicp_lev.ptr;
+        P.bicp_nlev = (const int*)s->bicp_nlev.ptr;
+    }
 }
 
 // Solves tile by tile; b and x are device arrays [n_dof][nrhs].
@@ -200,6 +210,7 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
     const int R = pick_tile(nrhs, o.rhs_tile);
     const int prec = o.precision;
     FE_TRY(check_system_precision(s, prec, "solve"));
+    FE_TRY(check_precond(ctx, s, o, "solve"));
     Workspace w;
     auto cleanup = [&]() { free_workspace(st, w); };
     fe_status e = alloc_workspace(st, n_dof, R, prec, 2 * ctx->num_sms, w);
@@ -318,6 +329,10 @@ fe_status job_create(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d
     }
     const int prec = o.precision;
     FE_TRY(check_system_precision(s, prec, "job"));
+    if (o.preconditioner != FE_PRECOND_BLOCK_JACOBI) {
+        set_error("job: multi-system launches use block Jacobi");
+        return FE_ERR_INVALID_ARG;
+    }
     SolveJob* j = new (std::nothrow) SolveJob();
     if (!j) {
         set_error("job: host allocation failed");
@@ -458,6 +473,30 @@ static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
         set_error("solve: bad tolerance or iteration limits");
         return FE_ERR_INVALID_ARG;
     }
+    if (out.preconditioner != FE_PRECOND_BLOCK_JACOBI && out.preconditioner != FE_PRECOND_BICP) {
+        set_error("solve: unknown preconditioner %d", (int)out.preconditioner);
+        return FE_ERR_INVALID_ARG;
+    }
+    if (out.preconditioner == FE_PRECOND_BICP && out.precision != FE_PREC_FP64) {
+        set_error("solve: the block incomplete Cholesky preconditioner runs with FE_PREC_FP64 only");
+        return FE_ERR_INVALID_ARG;
+    }
+    return FE_OK;
+}
+
+// A block incomplete Cholesky solve needs a factor with one band per CTA of
+// the solve grid (min(SMs, rows), the grid launch_solve uses).
+static fe_status check_precond(const fe_ctx* ctx, const fe_system* s, const fe_solve_opts& o, const char* what) {
+    if (o.preconditioner != FE_PRECOND_BICP) return FE_OK;
+    const int grid = std::min(ctx->num_sms, std::max(1, s->mesh->n_act));
+    if (s->bicp_n_sub < 1) {
+        set_error("%s: no block incomplete Cholesky factor (call fe_system_factor_bicp first)", what);
+        return FE_ERR_INVALID_ARG;
+    }
+    if (s->bicp_n_sub != grid) {
+        set_error("%s: the factor has %d bands, the solve runs %d CTAs", what, s->bicp_n_sub, grid);
+        return FE_ERR_INVALID_ARG;
+    }
     return FE_OK;
 }
 
@@ -477,6 +516,7 @@ void fe_solve_opts_default(fe_solve_opts* o) {
     o->rhs_tile = 0;
     o->max_pass_iter = 2000;
     o->wait_timeout_us = 4000000;
+    o->preconditioner = FE_PRECOND_BLOCK_JACOBI;
 }
 
 fe_status fe_solve_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b, int32_t b_on_device,
@@ -563,6 +603,7 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     FE_TRY(check_opts(o, opt));
     const int prec = opt.precision;
     FE_TRY(check_system_precision(s, prec, "fe_solve_rhs_noalloc"));
+    FE_TRY(check_precond(ctx, s, opt, "fe_solve_rhs_noalloc"));
     FE_CUDA(cudaSetDevice(ctx->device));
     char* base = nullptr;
     FE_TRY(static_scratch(ctx->device, &base));

@@ -80,6 +80,14 @@ struct SolveParams {
     unsigned long long* trace;  // optional [n_cta][kTraceIters][kTracePhases] timestamps
     unsigned long long timeout_ns;
     unsigned spin_ns;           // back-off between polls of the barrier generation
+    // block incomplete Cholesky factor, one band per CTA (FP64 solves; null:
+    // block Jacobi)
+    const double2* bicp_l;      // [nnzb * 9] L_IJ by block slot, row-major 3x3
+    const double2* bicp_linv;   // [n_rows * 9] L_II^{-1}
+    const int* bicp_tpos;       // [nnzb] slot of the transposed block
+    const int* bicp_order;      // [n_rows] band nodes by level
+    const int* bicp_lev;        // band b's level offsets at [first row + b, ...]
+    const int* bicp_nlev;       // [n_cta] levels per band
 };
 
 // ---------------------------------------------------------------------------
@@ -381,6 +389,90 @@ constexpr int kTraceStats = 8;
             P.trace[((size_t)cta * kTraceIters + trace_it) * kTracePhases + (k)] = globaltimer_ns(); \
     } while (0)
 
+// z = (L L^T)^{-1} r over the CTA's band of rows [r0, r1) (block incomplete
+// Cholesky, Section 3.1.5.3; Eq. 6): the forward substitution
+//     y_I = L_II^{-1} (r_I - sum_{r0 <= J < I} L_IJ y_J)
+// level by level, then the back substitution
+//     z_I = L_II^{-T} (y_I - sum_{I < J < r1} L_JI^T z_J)
+// in reverse level order, in place in z.  Nodes of one level do not couple;
+// a CTA barrier separates the levels.  One thread per (node, column); only
+// the columns with s_mask[c] != 0 are written.  r and z are written earlier
+// in this kernel, so they are read through the coherent path.
+template <int R>
+__device__ __noinline__ void bicp_apply(const SolveParams& P, const int cta, const int r0, const int r1,
+                                        const double2* rv, double2* z, const int* s_mask) {
+    const int tid = threadIdx.x;
+    const int nlev = P.bicp_nlev[cta];
+    const int* off = P.bicp_lev + r0 + cta;
+    const int* ord = P.bicp_order + r0;
+    for (int lv = 0; lv < nlev; ++lv) {
+        const int a = off[lv], n = (off[lv + 1] - a) * R;
+        for (int i = tid; i < n; i += kThreads) {
+            const int c = i % R;
+            if (!s_mask[c]) continue;
+            const int node = ord[a + i / R];
+            const size_t o = (size_t)3 * node * R + c;
+            double2 t0 = __ldcg(rv + o), t1 = __ldcg(rv + o + R), t2 = __ldcg(rv + o + 2 * R);
+            for (int p = __ldg(P.rp + node); p < __ldg(P.rp + node + 1); ++p) {
+                const int J = __ldg(P.col + p);
+                if (J >= node) break;
+                if (J < r0) continue;
+                const double2* L = P.bicp_l + (size_t)p * 9;
+                const size_t oj = (size_t)3 * J * R + c;
+                const double2 y0 = __ldcg(z + oj), y1 = __ldcg(z + oj + R), y2 = __ldcg(z + oj + 2 * R);
+                t0 = cfma(make_double2(-__ldg(&L[0].x), -__ldg(&L[0].y)), y0, t0);
+                t0 = cfma(make_double2(-__ldg(&L[1].x), -__ldg(&L[1].y)), y1, t0);
+                t0 = cfma(make_double2(-__ldg(&L[2].x), -__ldg(&L[2].y)), y2, t0);
+                t1 = cfma(make_double2(-__ldg(&L[3].x), -__ldg(&L[3].y)), y0, t1);
+                t1 = cfma(make_double2(-__ldg(&L[4].x), -__ldg(&L[4].y)), y1, t1);
+                t1 = cfma(make_double2(-__ldg(&L[5].x), -__ldg(&L[5].y)), y2, t1);
+                t2 = cfma(make_double2(-__ldg(&L[6].x), -__ldg(&L[6].y)), y0, t2);
+                t2 = cfma(make_double2(-__ldg(&L[7].x), -__ldg(&L[7].y)), y1, t2);
+                t2 = cfma(make_double2(-__ldg(&L[8].x), -__ldg(&L[8].y)), y2, t2);
+            }
+            const double2* M = P.bicp_linv + (size_t)node * 9;  // lower triangular
+            const double2 zero = make_double2(0.0, 0.0);
+            z[o] = cfma(__ldg(M + 0), t0, zero);
+            z[o + R] = cfma(__ldg(M + 4), t1, cfma(__ldg(M + 3), t0, zero));
+            z[o + 2 * R] = cfma(__ldg(M + 8), t2, cfma(__ldg(M + 7), t1, cfma(__ldg(M + 6), t0, zero)));
+        }
+        __syncthreads();
+    }
+    for (int lv = nlev - 1; lv >= 0; --lv) {
+        const int a = off[lv], n = (off[lv + 1] - a) * R;
+        for (int i = tid; i < n; i += kThreads) {
+            const int c = i % R;
+            if (!s_mask[c]) continue;
+            const int node = ord[a + i / R];
+            const size_t o = (size_t)3 * node * R + c;
+            double2 t0 = __ldcg(z + o), t1 = __ldcg(z + o + R), t2 = __ldcg(z + o + 2 * R);
+            for (int p = __ldg(P.rp + node + 1) - 1; p >= __ldg(P.rp + node); --p) {
+                const int J = __ldg(P.col + p);
+                if (J <= node) break;
+                if (J >= r1) continue;
+                const double2* L = P.bicp_l + (size_t)__ldg(P.bicp_tpos + p) * 9;  // block (J, I)
+                const size_t oj = (size_t)3 * J * R + c;
+                const double2 x0 = __ldcg(z + oj), x1 = __ldcg(z + oj + R), x2 = __ldcg(z + oj + 2 * R);
+                t0 = cfma(make_double2(-__ldg(&L[0].x), -__ldg(&L[0].y)), x0, t0);
+                t0 = cfma(make_double2(-__ldg(&L[3].x), -__ldg(&L[3].y)), x1, t0);
+                t0 = cfma(make_double2(-__ldg(&L[6].x), -__ldg(&L[6].y)), x2, t0);
+                t1 = cfma(make_double2(-__ldg(&L[1].x), -__ldg(&L[1].y)), x0, t1);
+                t1 = cfma(make_double2(-__ldg(&L[4].x), -__ldg(&L[4].y)), x1, t1);
+                t1 = cfma(make_double2(-__ldg(&L[7].x), -__ldg(&L[7].y)), x2, t1);
+                t2 = cfma(make_double2(-__ldg(&L[2].x), -__ldg(&L[2].y)), x0, t2);
+                t2 = cfma(make_double2(-__ldg(&L[5].x), -__ldg(&L[5].y)), x1, t2);
+                t2 = cfma(make_double2(-__ldg(&L[8].x), -__ldg(&L[8].y)), x2, t2);
+            }
+            const double2* M = P.bicp_linv + (size_t)node * 9;  // z = M^T t, M lower triangular
+            const double2 zero = make_double2(0.0, 0.0);
+            z[o] = cfma(__ldg(M + 6), t2, cfma(__ldg(M + 3), t1, cfma(__ldg(M + 0), t0, zero)));
+            z[o + R] = cfma(__ldg(M + 7), t2, cfma(__ldg(M + 4), t1, zero));
+            z[o + 2 * R] = cfma(__ldg(M + 8), t2, zero);
+        }
+        __syncthreads();
+    }
+}
+
 // Product phase of one CTA: optional TMA staging of its halo of uM, then the
 // products with NV fused dots.  Returns false when a bounded wait expired (the
 // error is recorded).
@@ -435,6 +527,9 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     C* pM = (C*)P.pM;
     const C* wv = (const C*)P.w;
     constexpr bool kSplit = !std::is_same<C, VT>::value;  // inner copies are separate buffers
+    // block incomplete Cholesky instead of block Jacobi (FP64 solves only)
+    constexpr bool kBicpType = std::is_same<TM, double>::value;
+    const bool bicp = kBicpType && P.bicp_l != nullptr;
 
     extern __shared__ __align__(128) char dyn[];
     double* s_red = (double*)dyn;
@@ -444,6 +539,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     __shared__ double s_in[kMaxNV * R], s_out[kMaxNV * R];
     __shared__ double s_bn[R], s_rr_ref[R], s_rel[R];
     __shared__ double s_gam_r[R], s_gam_i[R], s_al_r[R], s_al_i[R], s_be_r[R], s_be_i[R];
+    __shared__ int s_bmask[R];  // columns a block incomplete Cholesky application writes
     __shared__ int s_active[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_first[R], s_refresh[R],
         s_repl[R], s_pass_it[R];
     __shared__ int s_any_repl, s_any_active, s_any_refresh;
@@ -633,7 +729,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     }
                     s_exch[tid] = rv;
                     __syncthreads();
-                    if (valid) {
+                    if (valid && !bicp) {
                         const int node = r0 + i / (3 * R);
                         const int al = (i / R) % 3;
                         const double2* drow = P.dinv64 + (size_t)node * 9 + 3 * al;
@@ -644,6 +740,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                         if (kSplit) uM[o] = from_c128<C>(uu);
                     }
                     __syncthreads();
+                }
+                if constexpr (kBicpType) {
+                    if (bicp) {
+                        if (tid < R) s_bmask[tid] = s_repl[tid] && s_active[tid];
+                        __syncthreads();
+                        bicp_apply<R>(P, cta, r0, r1, P.r, P.u, s_bmask);
+                    }
                 }
             }
             if (tid == 0) {
@@ -848,7 +951,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                 }
                 s_exch[tid] = rn;
                 __syncthreads();
-                if (valid) {
+                if (valid && !bicp) {
                     const int node = r0 + i / (3 * R);
                     const int al = (i / R) % 3;
                     const double2* drow = P.dinv64 + (size_t)node * 9 + 3 * al;
@@ -859,6 +962,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     if (kSplit) uM[o] = from_c128<C>(uu);
                 }
                 __syncthreads();
+            }
+            if constexpr (kBicpType) {
+                if (bicp) {
+                    if (tid < R) s_bmask[tid] = s_active[tid] && !s_repl[tid];
+                    __syncthreads();
+                    bicp_apply<R>(P, cta, r0, r1, P.r, P.u, s_bmask);
+                }
             }
         }
         FE_TRACE_MARK(6);

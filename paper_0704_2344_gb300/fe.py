@@ -27,6 +27,7 @@ FE_VARIANT_S, FE_VARIANT_L, FE_VARIANT_P = 0, 1, 2
 FE_PREC_FP64, FE_PREC_MIXED, FE_PREC_DF = 0, 1, 2
 FE_BOUNDARY_ABC, FE_BOUNDARY_SYMMETRY, FE_BOUNDARY_ANTISYMMETRY = 0, 1, 2
 FE_FORMULATION_H, FE_FORMULATION_E = 0, 1
+FE_PRECOND_BLOCK_JACOBI, FE_PRECOND_BICP = 0, 1
 
 LIB_PATH = Path(__file__).resolve().parent / "libfe_gb300.so"
 
@@ -71,7 +72,7 @@ class fe_planewave(C.Structure):
 class fe_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32),
-                ("max_pass_iter", C.c_int32), ("wait_timeout_us", C.c_int32)]
+                ("max_pass_iter", C.c_int32), ("wait_timeout_us", C.c_int32), ("preconditioner", C.c_int32)]
 
 
 class fe_solve_stats(C.Structure):
@@ -132,6 +133,8 @@ def load() -> C.CDLL:
         "fe_assemble": (C.c_int, [P, P, C.c_double, C.c_int32, C.POINTER(P)]),
         "fe_system_export": (C.c_int, [P, P, P, P, P]),
         "fe_system_export_df": (C.c_int, [P, P, P]),
+        "fe_system_factor_bicp": (C.c_int, [P, P, C.c_int32]),
+        "fe_system_export_bicp": (C.c_int, [P, P, P, P]),
         "fe_system_info": (C.c_int, [P, C.POINTER(fe_system_stats)]),
         "fe_system_destroy": (None, [P]),
         "fe_rhs": (C.c_int, [P, P, C.c_int32, C.POINTER(fe_planewave), P, C.c_int32]),
@@ -327,6 +330,24 @@ def fe_system_export_df(ctx, system, mesh) -> np.ndarray:
     return a
 
 
+def fe_system_factor_bicp(ctx, system, n_sub: int = 0) -> int:
+    """Builds the block incomplete Cholesky factor (n_sub bands; 0 = one per
+    CTA of the solve grid) and returns the number of bands."""
+    _check(load().fe_system_factor_bicp(ctx, system, int(n_sub)), "fe_system_factor_bicp")
+    n = C.c_int32(0)
+    _check(load().fe_system_export_bicp(ctx, system, None, C.byref(n)), "fe_system_export_bicp")
+    return int(n.value)
+
+
+def fe_system_export_bicp(ctx, system, mesh):
+    """(L [nnzb, 3, 3] complex128 by block slot, number of bands)."""
+    info = fe_mesh_info(mesh)
+    a = np.empty((info["nnzb"], 3, 3), np.complex128)
+    n = C.c_int32(0)
+    _check(load().fe_system_export_bicp(ctx, system, _ptr(a), C.byref(n)), "fe_system_export_bicp")
+    return a, int(n.value)
+
+
 def fe_system_destroy(system):
     load().fe_system_destroy(system)
 
@@ -359,7 +380,8 @@ def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
 
 
 def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
-               rhs_tile=0, max_pass_iter=None, wait_timeout_us=None) -> fe_solve_opts:
+               rhs_tile=0, max_pass_iter=None, wait_timeout_us=None,
+               preconditioner=FE_PRECOND_BLOCK_JACOBI) -> fe_solve_opts:
     o = fe_solve_opts()
     load().fe_solve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
@@ -368,6 +390,7 @@ def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, m
         o.max_pass_iter = int(max_pass_iter)
     if wait_timeout_us is not None:
         o.wait_timeout_us = int(wait_timeout_us)
+    o.preconditioner = int(preconditioner)
     return o
 
 

@@ -37,8 +37,10 @@ def test_nm_exports(fe):
 def test_option_defaults_without_gpu(fe):
     import ctypes
     o = fe.fe_solve_opts()
+    o.preconditioner = 77                       # the C default writes the struct's last field too
     fe.load().fe_solve_opts_default(ctypes.byref(o))
     assert o.precision == fe.FE_PREC_DF and o.tol == 1e-8 and o.max_iter == 100000 and o.max_pass_iter == 2000
+    assert o.preconditioner == fe.FE_PRECOND_BLOCK_JACOBI
     s = fe.fe_serve_opts()
     fe.load().fe_serve_opts_default(ctypes.byref(s))
     assert s.precision == fe.FE_PREC_DF and s.tol == 1e-8 and s.work_per_cta == 2048
