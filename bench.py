@@ -268,9 +268,11 @@ def run_ours(args, rank, world, local_rank, precision_name):
     info = fe.fe_mesh_info(mesh0)
     sys0 = fe.fe_assemble(ctx, mesh0, prob.freq_hz, precision)
     sysinfo = fe.fe_system_info(sys0)
-    bicp_blocks = 0
+    bicp_blocks, bicp_factor_ms = 0, None
     if bicp:  # strictly lower blocks inside the bands: the substitutions' work
-        n_band = fe.fe_system_factor_bicp(ctx, sys0, 0)
+        t_f = time.perf_counter()
+        n_band = fe.fe_system_factor_bicp(ctx, sys0, 0)   # returns after the device finished
+        bicp_factor_ms = (time.perf_counter() - t_f) * 1e3
         mp = fe.fe_mesh_export_maps(ctx, mesh0)
         rows = np.repeat(np.arange(info["n_nodes"]), np.diff(mp["row_ptr"]))
         band = np.searchsorted((np.arange(n_band + 1) * info["n_nodes"]) // n_band, np.arange(info["n_nodes"]),
@@ -342,6 +344,7 @@ def run_ours(args, rank, world, local_rank, precision_name):
                                        product_rows(sysinfo, base)))}
     if bicp:
         common["bicp_band_blocks"] = bicp_blocks
+        common["bicp_factor_ms"] = round(bicp_factor_ms, 3)
     if base == "fp64":
         # the complex128 products run on the FP64 pipes (1/64 of the FP32 rate on GB300): ALU-bound
         achieved = (fl_prod + fl64) / secs / 1e12 if secs > 0 else None
@@ -745,7 +748,10 @@ def main():
     line = dict(lines[best])
     line["modes"] = {m: {k: lines[m][k] for k in ("value", "ms_per_step", "converged", "iterations_per_solve",
                                                    "refinement_passes_per_solve", "final_rel_residual", "dtype")}
-                     | {"roofline_frac": lines[m]["roofline"]["frac"], "bound": lines[m]["roofline"]["bound"]}
+                     | {"roofline_frac": lines[m]["roofline"]["frac"], "bound": lines[m]["roofline"]["bound"],
+                        "solve_kernel_ms": lines[m]["roofline"]["launch_ms"]}
+                     | ({"bicp_factor_ms": lines[m]["roofline"]["bicp_factor_ms"]}
+                        if "bicp_factor_ms" in lines[m]["roofline"] else {})
                      for m in modes}
     if rank == 0:
         if not args.no_cpu_baseline and world == 1:

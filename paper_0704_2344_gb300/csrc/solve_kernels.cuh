@@ -395,79 +395,98 @@ constexpr int kTraceStats = 8;
 // level by level, then the back substitution
 //     z_I = L_II^{-T} (y_I - sum_{I < J < r1} L_JI^T z_J)
 // in reverse level order, in place in z.  Nodes of one level do not couple;
-// a CTA barrier separates the levels.  One thread per (node, column); only
-// the columns with s_mask[c] != 0 are written.  r and z are written earlier
-// in this kernel, so they are read through the coherent path.
+// a CTA barrier separates the levels.  One warp per (node, column): lane k
+// takes the row's k-th block (a row has at most 27), so the block loads of a
+// node are issued together, and a fixed butterfly sums the lanes.  Only the
+// columns with s_mask[c] != 0 are written.  r and z are written earlier in
+// this kernel, so they are read through the coherent path.
+__device__ __forceinline__ double2 warp_csum(double2 v) {
+#pragma unroll
+    for (int m = 16; m >= 1; m >>= 1) {
+        v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
+        v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
+    }
+    return v;
+}
+
 template <int R>
 __device__ __noinline__ void bicp_apply(const SolveParams& P, const int cta, const int r0, const int r1,
                                         const double2* rv, double2* z, const int* s_mask) {
-    const int tid = threadIdx.x;
+    constexpr int kWarps = kThreads / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nlev = P.bicp_nlev[cta];
     const int* off = P.bicp_lev + r0 + cta;
     const int* ord = P.bicp_order + r0;
+    const double2 zero = make_double2(0.0, 0.0);
     for (int lv = 0; lv < nlev; ++lv) {
         const int a = off[lv], n = (off[lv + 1] - a) * R;
-        for (int i = tid; i < n; i += kThreads) {
+        for (int i = warp; i < n; i += kWarps) {
             const int c = i % R;
-            if (!s_mask[c]) continue;
+            if (!s_mask[c]) continue;  // uniform over the warp
             const int node = ord[a + i / R];
             const size_t o = (size_t)3 * node * R + c;
-            double2 t0 = __ldcg(rv + o), t1 = __ldcg(rv + o + R), t2 = __ldcg(rv + o + 2 * R);
-            for (int p = __ldg(P.rp + node); p < __ldg(P.rp + node + 1); ++p) {
+            double2 t0 = zero, t1 = zero, t2 = zero;
+            const int p = __ldg(P.rp + node) + lane;
+            if (p < __ldg(P.rp + node + 1)) {
                 const int J = __ldg(P.col + p);
-                if (J >= node) break;
-                if (J < r0) continue;
-                const double2* L = P.bicp_l + (size_t)p * 9;
-                const size_t oj = (size_t)3 * J * R + c;
-                const double2 y0 = __ldcg(z + oj), y1 = __ldcg(z + oj + R), y2 = __ldcg(z + oj + 2 * R);
-                t0 = cfma(make_double2(-__ldg(&L[0].x), -__ldg(&L[0].y)), y0, t0);
-                t0 = cfma(make_double2(-__ldg(&L[1].x), -__ldg(&L[1].y)), y1, t0);
-                t0 = cfma(make_double2(-__ldg(&L[2].x), -__ldg(&L[2].y)), y2, t0);
-                t1 = cfma(make_double2(-__ldg(&L[3].x), -__ldg(&L[3].y)), y0, t1);
-                t1 = cfma(make_double2(-__ldg(&L[4].x), -__ldg(&L[4].y)), y1, t1);
-                t1 = cfma(make_double2(-__ldg(&L[5].x), -__ldg(&L[5].y)), y2, t1);
-                t2 = cfma(make_double2(-__ldg(&L[6].x), -__ldg(&L[6].y)), y0, t2);
-                t2 = cfma(make_double2(-__ldg(&L[7].x), -__ldg(&L[7].y)), y1, t2);
-                t2 = cfma(make_double2(-__ldg(&L[8].x), -__ldg(&L[8].y)), y2, t2);
+                if (J >= r0 && J < node) {
+                    const double2* L = P.bicp_l + (size_t)p * 9;
+                    const size_t oj = (size_t)3 * J * R + c;
+                    const double2 y0 = __ldcg(z + oj), y1 = __ldcg(z + oj + R), y2 = __ldcg(z + oj + 2 * R);
+                    t0 = cfma(__ldg(L + 2), y2, cfma(__ldg(L + 1), y1, cfma(__ldg(L + 0), y0, zero)));
+                    t1 = cfma(__ldg(L + 5), y2, cfma(__ldg(L + 4), y1, cfma(__ldg(L + 3), y0, zero)));
+                    t2 = cfma(__ldg(L + 8), y2, cfma(__ldg(L + 7), y1, cfma(__ldg(L + 6), y0, zero)));
+                }
             }
-            const double2* M = P.bicp_linv + (size_t)node * 9;  // lower triangular
-            const double2 zero = make_double2(0.0, 0.0);
-            z[o] = cfma(__ldg(M + 0), t0, zero);
-            z[o + R] = cfma(__ldg(M + 4), t1, cfma(__ldg(M + 3), t0, zero));
-            z[o + 2 * R] = cfma(__ldg(M + 8), t2, cfma(__ldg(M + 7), t1, cfma(__ldg(M + 6), t0, zero)));
+            t0 = warp_csum(t0);
+            t1 = warp_csum(t1);
+            t2 = warp_csum(t2);
+            if (lane == 0) {
+                const double2 b0 = __ldcg(rv + o), b1 = __ldcg(rv + o + R), b2 = __ldcg(rv + o + 2 * R);
+                t0 = make_double2(b0.x - t0.x, b0.y - t0.y);
+                t1 = make_double2(b1.x - t1.x, b1.y - t1.y);
+                t2 = make_double2(b2.x - t2.x, b2.y - t2.y);
+                const double2* M = P.bicp_linv + (size_t)node * 9;  // lower triangular
+                z[o] = cfma(__ldg(M + 0), t0, zero);
+                z[o + R] = cfma(__ldg(M + 4), t1, cfma(__ldg(M + 3), t0, zero));
+                z[o + 2 * R] = cfma(__ldg(M + 8), t2, cfma(__ldg(M + 7), t1, cfma(__ldg(M + 6), t0, zero)));
+            }
         }
         __syncthreads();
     }
     for (int lv = nlev - 1; lv >= 0; --lv) {
         const int a = off[lv], n = (off[lv + 1] - a) * R;
-        for (int i = tid; i < n; i += kThreads) {
+        for (int i = warp; i < n; i += kWarps) {
             const int c = i % R;
             if (!s_mask[c]) continue;
             const int node = ord[a + i / R];
             const size_t o = (size_t)3 * node * R + c;
-            double2 t0 = __ldcg(z + o), t1 = __ldcg(z + o + R), t2 = __ldcg(z + o + 2 * R);
-            for (int p = __ldg(P.rp + node + 1) - 1; p >= __ldg(P.rp + node); --p) {
+            double2 t0 = zero, t1 = zero, t2 = zero;
+            const int p = __ldg(P.rp + node) + lane;
+            if (p < __ldg(P.rp + node + 1)) {
                 const int J = __ldg(P.col + p);
-                if (J <= node) break;
-                if (J >= r1) continue;
-                const double2* L = P.bicp_l + (size_t)__ldg(P.bicp_tpos + p) * 9;  // block (J, I)
-                const size_t oj = (size_t)3 * J * R + c;
-                const double2 x0 = __ldcg(z + oj), x1 = __ldcg(z + oj + R), x2 = __ldcg(z + oj + 2 * R);
-                t0 = cfma(make_double2(-__ldg(&L[0].x), -__ldg(&L[0].y)), x0, t0);
-                t0 = cfma(make_double2(-__ldg(&L[3].x), -__ldg(&L[3].y)), x1, t0);
-                t0 = cfma(make_double2(-__ldg(&L[6].x), -__ldg(&L[6].y)), x2, t0);
-                t1 = cfma(make_double2(-__ldg(&L[1].x), -__ldg(&L[1].y)), x0, t1);
-                t1 = cfma(make_double2(-__ldg(&L[4].x), -__ldg(&L[4].y)), x1, t1);
-                t1 = cfma(make_double2(-__ldg(&L[7].x), -__ldg(&L[7].y)), x2, t1);
-                t2 = cfma(make_double2(-__ldg(&L[2].x), -__ldg(&L[2].y)), x0, t2);
-                t2 = cfma(make_double2(-__ldg(&L[5].x), -__ldg(&L[5].y)), x1, t2);
-                t2 = cfma(make_double2(-__ldg(&L[8].x), -__ldg(&L[8].y)), x2, t2);
+                if (J > node && J < r1) {
+                    const double2* L = P.bicp_l + (size_t)__ldg(P.bicp_tpos + p) * 9;  // block (J, I)
+                    const size_t oj = (size_t)3 * J * R + c;
+                    const double2 x0 = __ldcg(z + oj), x1 = __ldcg(z + oj + R), x2 = __ldcg(z + oj + 2 * R);
+                    t0 = cfma(__ldg(L + 6), x2, cfma(__ldg(L + 3), x1, cfma(__ldg(L + 0), x0, zero)));
+                    t1 = cfma(__ldg(L + 7), x2, cfma(__ldg(L + 4), x1, cfma(__ldg(L + 1), x0, zero)));
+                    t2 = cfma(__ldg(L + 8), x2, cfma(__ldg(L + 5), x1, cfma(__ldg(L + 2), x0, zero)));
+                }
             }
-            const double2* M = P.bicp_linv + (size_t)node * 9;  // z = M^T t, M lower triangular
-            const double2 zero = make_double2(0.0, 0.0);
-            z[o] = cfma(__ldg(M + 6), t2, cfma(__ldg(M + 3), t1, cfma(__ldg(M + 0), t0, zero)));
-            z[o + R] = cfma(__ldg(M + 7), t2, cfma(__ldg(M + 4), t1, zero));
-            z[o + 2 * R] = cfma(__ldg(M + 8), t2, zero);
+            t0 = warp_csum(t0);
+            t1 = warp_csum(t1);
+            t2 = warp_csum(t2);
+            if (lane == 0) {
+                const double2 y0 = __ldcg(z + o), y1 = __ldcg(z + o + R), y2 = __ldcg(z + o + 2 * R);
+                t0 = make_double2(y0.x - t0.x, y0.y - t0.y);
+                t1 = make_double2(y1.x - t1.x, y1.y - t1.y);
+                t2 = make_double2(y2.x - t2.x, y2.y - t2.y);
+                const double2* M = P.bicp_linv + (size_t)node * 9;  // z = M^T t, M lower triangular
+                z[o] = cfma(__ldg(M + 6), t2, cfma(__ldg(M + 3), t1, cfma(__ldg(M + 0), t0, zero)));
+                z[o + R] = cfma(__ldg(M + 7), t2, cfma(__ldg(M + 4), t1, zero));
+                z[o + 2 * R] = cfma(__ldg(M + 8), t2, zero);
+            }
         }
         __syncthreads();
     }
