@@ -410,7 +410,7 @@ static void system_free(fe_system* s) {
     cudaStream_t st = s->ctx->stream;
     for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
                       &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->bicp_l,
-                      &s->bicp_linv, &s->bicp_tpos, &s->bicp_order, &s->bicp_lev, &s->bicp_nlev})
+                      &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         dev_free(st, *b);
     s->bicp_n_sub = 0;
 }
@@ -588,7 +588,7 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
     int64_t bytes = 0;
     for (const DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
                             &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->bicp_l,
-                            &s->bicp_linv, &s->bicp_tpos, &s->bicp_order, &s->bicp_lev, &s->bicp_nlev})
+                            &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         bytes += (int64_t)b->bytes;
     out->device_bytes = bytes;
     return FE_OK;

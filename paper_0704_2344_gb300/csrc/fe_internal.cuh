@@ -187,7 +187,8 @@ struct fe_system {
                                      //   (J < I in I's band; L_II lower triangular; zero elsewhere)
     fe::DevBuf bicp_linv;            // double2 [n_act * 9]: L_II^{-1} (lower triangular)
     fe::DevBuf bicp_tpos;            // int [nnzb]: slot of block (J, I) for the block (I, J)
-    fe::DevBuf bicp_order;           // int [n_act]: each band's nodes sorted by level, in the band's range
+    fe::DevBuf bicp_tab;             // int4 [n_act]: each band's nodes sorted by level, in the band's range:
+                                     //   (node, first slot in the band, diagonal slot, end of the band's slots)
     fe::DevBuf bicp_lev;             // int [n_act + n_sub]: band b's level offsets at [first node + b, ...]
     fe::DevBuf bicp_nlev;            // int [n_sub]: levels per band
 };

@@ -76,9 +76,11 @@ __global__ void k_bicp_tpos(int n, const int* __restrict__ rp, const int* __rest
     }
 }
 
-// Levels and the level-sorted node order of each band.
+// Levels and the level-sorted node table of each band: (node, first slot of
+// the row inside the band, diagonal slot, end of the row's slots inside the
+// band), so the substitutions reach a row's band blocks without searching.
 __global__ void k_bicp_levels(int n, int S, const int* __restrict__ rp, const int* __restrict__ col,
-                              int* __restrict__ lvl, int* __restrict__ order, int* __restrict__ lev,
+                              int* __restrict__ lvl, int4* __restrict__ tab, int* __restrict__ lev,
                               int* __restrict__ nlev) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= S) return;
@@ -100,7 +102,16 @@ __global__ void k_bicp_levels(int n, int S, const int* __restrict__ rp, const in
     for (int l = 0; l <= nl; ++l) off[l] = 0;
     for (int I = i0; I < i1; ++I) off[lvl[I] + 1] += 1;
     for (int l = 1; l <= nl; ++l) off[l] += off[l - 1];
-    for (int I = i0; I < i1; ++I) order[i0 + off[lvl[I]]++] = I;  // off[l] ends at the start of level l + 1
+    for (int I = i0; I < i1; ++I) {
+        int lo = rp[I + 1], dg = -1, hi = rp[I + 1];
+        for (int p = rp[I + 1] - 1; p >= rp[I]; --p) {
+            const int J = col[p];
+            if (J >= i1) hi = p;
+            if (J >= i0) lo = p;
+            if (J == I) dg = p;
+        }
+        tab[i0 + off[lvl[I]]++] = make_int4(I, lo, dg, hi);  // off[l] ends at the start of level l + 1
+    }
     for (int l = nl; l >= 1; --l) off[l] = off[l - 1];
     off[0] = 0;
     nlev[b] = nl;
@@ -233,13 +244,13 @@ fe_status fe_system_factor_bicp(fe_ctx* ctx, fe_system* s, int32_t n_sub) {
     }
     FE_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    for (DevBuf* b : {&s->bicp_l, &s->bicp_linv, &s->bicp_tpos, &s->bicp_order, &s->bicp_lev, &s->bicp_nlev})
+    for (DevBuf* b : {&s->bicp_l, &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         dev_free(st, *b);
     s->bicp_n_sub = 0;
     DevBuf lvl, status;
     auto fail = [&](fe_status e) {
-        for (DevBuf* b : {&s->bicp_l, &s->bicp_linv, &s->bicp_tpos, &s->bicp_order, &s->bicp_lev, &s->bicp_nlev,
-                          &lvl, &status})
+        for (DevBuf* b : {&s->bicp_l, &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev, &lvl,
+                          &status})
             dev_free(st, *b);
         return e;
     };
@@ -248,7 +259,7 @@ fe_status fe_system_factor_bicp(fe_ctx* ctx, fe_system* s, int32_t n_sub) {
     if ((e = dev_alloc(st, s->bicp_l, nb * 9 * sizeof(double2))) != FE_OK) return fail(e);
     if ((e = dev_alloc(st, s->bicp_linv, (size_t)n * 9 * sizeof(double2))) != FE_OK) return fail(e);
     if ((e = dev_alloc(st, s->bicp_tpos, nb * sizeof(int))) != FE_OK) return fail(e);
-    if ((e = dev_alloc(st, s->bicp_order, (size_t)n * sizeof(int))) != FE_OK) return fail(e);
+    if ((e = dev_alloc(st, s->bicp_tab, (size_t)n * sizeof(int4))) != FE_OK) return fail(e);
     if ((e = dev_alloc(st, s->bicp_lev, ((size_t)n + S) * sizeof(int))) != FE_OK) return fail(e);
     if ((e = dev_alloc(st, s->bicp_nlev, (size_t)S * sizeof(int))) != FE_OK) return fail(e);
     if ((e = dev_alloc(st, lvl, (size_t)n * sizeof(int))) != FE_OK) return fail(e);
@@ -263,7 +274,7 @@ fe_status fe_system_factor_bicp(fe_ctx* ctx, fe_system* s, int32_t n_sub) {
     }
     k_bicp_tpos<<<blocks_of(n, 128), 128, 0, st>>>(n, rp, col, (int*)s->bicp_tpos.ptr, (int*)status.ptr);
     count_launches(1);
-    k_bicp_levels<<<blocks_of(S, 32), 32, 0, st>>>(n, S, rp, col, (int*)lvl.ptr, (int*)s->bicp_order.ptr,
+    k_bicp_levels<<<blocks_of(S, 32), 32, 0, st>>>(n, S, rp, col, (int*)lvl.ptr, (int4*)s->bicp_tab.ptr,
                                                    (int*)s->bicp_lev.ptr, (int*)s->bicp_nlev.ptr);
     count_launches(1);
     k_bicp_factor<<<blocks_of(S, 32), 32, 0, st>>>(n, S, rp, col, (const double2*)s->val64.ptr, s->stride,

@@ -195,7 +195,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
         P.bicp_l = (const double2*)s->bicp_l.ptr;
         P.bicp_linv = (const double2*)s->bicp_linv.ptr;
         P.bicp_tpos = (const int*)s->bicp_tpos.ptr;
-        P.bicp_order = (const int*)s->bicp_order.ptr;
+        P.bicp_tab = (const int4*)s->bicp_tab.ptr;
         P.bicp_lev = (const int*)s->bicp_lev.ptr;
         P.bicp_nlev = (const int*)s->bicp_nlev.ptr;
     }

@@ -85,7 +85,7 @@ struct SolveParams {
     const double2* bicp_l;      // [nnzb * 9] L_IJ by block slot, row-major 3x3
     const double2* bicp_linv;   // [n_rows * 9] L_II^{-1}
     const int* bicp_tpos;       // [nnzb] slot of the transposed block
-    const int* bicp_order;      // [n_rows] band nodes by level
+    const int4* bicp_tab;       // [n_rows] band nodes by level: (node, first band slot, diagonal slot, band end)
     const int* bicp_lev;        // band b's level offsets at [first row + b, ...]
     const int* bicp_nlev;       // [n_cta] levels per band
 };
@@ -389,106 +389,105 @@ constexpr int kTraceStats = 8;
             P.trace[((size_t)cta * kTraceIters + trace_it) * kTracePhases + (k)] = globaltimer_ns(); \
     } while (0)
 
-// z = (L L^T)^{-1} r over the CTA's band of rows [r0, r1) (block incomplete
-// Cholesky, Section 3.1.5.3; Eq. 6): the forward substitution
-//     y_I = L_II^{-1} (r_I - sum_{r0 <= J < I} L_IJ y_J)
+// z = (L L^T)^{-1} r over the CTA's band of rows (block incomplete Cholesky,
+// Section 3.1.5.3; Eq. 6): the forward substitution
+//     y_I = L_II^{-1} (r_I - sum_{J < I in the band} L_IJ y_J)
 // level by level, then the back substitution
-//     z_I = L_II^{-T} (y_I - sum_{I < J < r1} L_JI^T z_J)
+//     z_I = L_II^{-T} (y_I - sum_{J > I in the band} L_JI^T z_J)
 // in reverse level order, in place in z.  Nodes of one level do not couple;
-// a CTA barrier separates the levels.  One warp per (node, column): lane k
-// takes the row's k-th block (a row has at most 27), so the block loads of a
-// node are issued together, and a fixed butterfly sums the lanes.  Only the
-// columns with s_mask[c] != 0 are written.  r and z are written earlier in
-// this kernel, so they are read through the coherent path.
-__device__ __forceinline__ double2 warp_csum(double2 v) {
+// a CTA barrier separates the levels.  One half-warp per (node, column):
+// lane k takes the k-th band block on its side of the diagonal (at most 13
+// on each side of a 27-point row; the node table gives the slot ranges, and
+// the back substitution finds L_JI at the transposed slot, where the forward
+// pass has just read it), so a node's block loads are issued together, and a
+// fixed butterfly sums the lanes.  Only the columns with s_mask[c] != 0
+// are written.  r and z are written earlier in this kernel, so they are read
+// through the coherent path.
+__device__ __forceinline__ double2 half_warp_csum(double2 v) {
 #pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
+    for (int m = 8; m >= 1; m >>= 1) {
         v.x += __shfl_xor_sync(0xffffffffu, v.x, m);
         v.y += __shfl_xor_sync(0xffffffffu, v.y, m);
     }
     return v;
 }
 
-template <int R>
-__device__ __noinline__ void bicp_apply(const SolveParams& P, const int cta, const int r0, const int r1,
-                                        const double2* rv, double2* z, const int* s_mask) {
-    constexpr int kWarps = kThreads / 32;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int nlev = P.bicp_nlev[cta];
-    const int* off = P.bicp_lev + r0 + cta;
-    const int* ord = P.bicp_order + r0;
+// t = L v (kTrans = false) or L^T v (true) for one 3x3 block
+template <bool kTrans>
+__device__ __forceinline__ void block_times(const double2* __restrict__ L, double2 v0, double2 v1, double2 v2,
+                                            double2& t0, double2& t1, double2& t2) {
     const double2 zero = make_double2(0.0, 0.0);
-    for (int lv = 0; lv < nlev; ++lv) {
-        const int a = off[lv], n = (off[lv + 1] - a) * R;
-        for (int i = warp; i < n; i += kWarps) {
-            const int c = i % R;
-            if (!s_mask[c]) continue;  // uniform over the warp
-            const int node = ord[a + i / R];
-            const size_t o = (size_t)3 * node * R + c;
-            double2 t0 = zero, t1 = zero, t2 = zero;
-            const int p = __ldg(P.rp + node) + lane;
-            if (p < __ldg(P.rp + node + 1)) {
-                const int J = __ldg(P.col + p);
-                if (J >= r0 && J < node) {
-                    const double2* L = P.bicp_l + (size_t)p * 9;
-                    const size_t oj = (size_t)3 * J * R + c;
-                    const double2 y0 = __ldcg(z + oj), y1 = __ldcg(z + oj + R), y2 = __ldcg(z + oj + 2 * R);
-                    t0 = cfma(__ldg(L + 2), y2, cfma(__ldg(L + 1), y1, cfma(__ldg(L + 0), y0, zero)));
-                    t1 = cfma(__ldg(L + 5), y2, cfma(__ldg(L + 4), y1, cfma(__ldg(L + 3), y0, zero)));
-                    t2 = cfma(__ldg(L + 8), y2, cfma(__ldg(L + 7), y1, cfma(__ldg(L + 6), y0, zero)));
+    constexpr int a = kTrans ? 3 : 1, b = kTrans ? 1 : 3;  // strides along v and along t
+    t0 = cfma(__ldg(L + 2 * a), v2, cfma(__ldg(L + a), v1, cfma(__ldg(L + 0), v0, zero)));
+    t1 = cfma(__ldg(L + b + 2 * a), v2, cfma(__ldg(L + b + a), v1, cfma(__ldg(L + b), v0, zero)));
+    t2 = cfma(__ldg(L + 2 * b + 2 * a), v2, cfma(__ldg(L + 2 * b + a), v1, cfma(__ldg(L + 2 * b), v0, zero)));
+}
+
+template <int R>
+__device__ __noinline__ void bicp_apply(const SolveParams& P, const int cta, const int r0, const double2* rv,
+                                        double2* z, const int* s_mask) {
+    constexpr int kItems = kThreads / 16;  // (node, column) items per pass
+    const int sub = threadIdx.x & 15, item = threadIdx.x >> 4;
+    const int nlev = __ldg(P.bicp_nlev + cta);
+    const int* off = P.bicp_lev + r0 + cta;
+    const int4* tab = P.bicp_tab + r0;
+    const double2 zero = make_double2(0.0, 0.0);
+    for (int pass = 0; pass < 2; ++pass) {  // 0: forward, 1: back
+        for (int k = 0; k < nlev; ++k) {
+            const int lv = pass == 0 ? k : nlev - 1 - k;
+            const int a = __ldg(off + lv), n = (__ldg(off + lv + 1) - a) * R;
+            // a warp holds items 2w and 2w + 1; warps with neither leave (the
+            // condition is uniform over the warp, so its shuffles stay converged)
+            for (int base = 0; base + (item & ~1) < n; base += kItems) {
+                const int i = base + item;
+                const int c = i % R;
+                const bool on = i < n && s_mask[c] != 0;
+                double2 t0 = zero, t1 = zero, t2 = zero, b0 = zero, b1 = zero, b2 = zero;
+                size_t o = 0;
+                int node = 0;
+                if (on) {
+                    const int4 e = __ldg(tab + a + i / R);
+                    node = e.x;
+                    o = (size_t)3 * node * R + c;
+                    if (sub == 0) {  // the node's own values, needed after the sum
+                        const double2* own = pass == 0 ? rv : z;
+                        b0 = __ldcg(own + o);
+                        b1 = __ldcg(own + o + R);
+                        b2 = __ldcg(own + o + 2 * R);
+                    }
+                    const int p = (pass == 0 ? e.y : e.z + 1) + sub;
+                    if (p < (pass == 0 ? e.z : e.w)) {
+                        const int J = __ldg(P.col + p);
+                        const size_t oj = (size_t)3 * J * R + c;
+                        if (pass == 0)
+                            block_times<false>(P.bicp_l + (size_t)p * 9, __ldcg(z + oj), __ldcg(z + oj + R),
+                                               __ldcg(z + oj + 2 * R), t0, t1, t2);
+                        else  // L_JI^T z_J
+                            block_times<true>(P.bicp_l + (size_t)__ldg(P.bicp_tpos + p) * 9, __ldcg(z + oj),
+                                              __ldcg(z + oj + R), __ldcg(z + oj + 2 * R), t0, t1, t2);
+                    }
+                }
+                t0 = half_warp_csum(t0);
+                t1 = half_warp_csum(t1);
+                t2 = half_warp_csum(t2);
+                if (on && sub == 0) {
+                    t0 = make_double2(b0.x - t0.x, b0.y - t0.y);
+                    t1 = make_double2(b1.x - t1.x, b1.y - t1.y);
+                    t2 = make_double2(b2.x - t2.x, b2.y - t2.y);
+                    const double2* M = P.bicp_linv + (size_t)node * 9;  // lower triangular
+                    if (pass == 0) {  // z = M t
+                        z[o] = cfma(__ldg(M + 0), t0, zero);
+                        z[o + R] = cfma(__ldg(M + 4), t1, cfma(__ldg(M + 3), t0, zero));
+                        z[o + 2 * R] = cfma(__ldg(M + 8), t2, cfma(__ldg(M + 7), t1, cfma(__ldg(M + 6), t0, zero)));
+                    } else {  // z = M^T t
+                        z[o] = cfma(__ldg(M + 6), t2, cfma(__ldg(M + 3), t1, cfma(__ldg(M + 0), t0, zero)));
+                        z[o + R] = cfma(__ldg(M + 7), t2, cfma(__ldg(M + 4), t1, zero));
+                        z[o + 2 * R] = cfma(__ldg(M + 8), t2, zero);
+                    }
                 }
             }
-            t0 = warp_csum(t0);
-            t1 = warp_csum(t1);
-            t2 = warp_csum(t2);
-            if (lane == 0) {
-                const double2 b0 = __ldcg(rv + o), b1 = __ldcg(rv + o + R), b2 = __ldcg(rv + o + 2 * R);
-                t0 = make_double2(b0.x - t0.x, b0.y - t0.y);
-                t1 = make_double2(b1.x - t1.x, b1.y - t1.y);
-                t2 = make_double2(b2.x - t2.x, b2.y - t2.y);
-                const double2* M = P.bicp_linv + (size_t)node * 9;  // lower triangular
-                z[o] = cfma(__ldg(M + 0), t0, zero);
-                z[o + R] = cfma(__ldg(M + 4), t1, cfma(__ldg(M + 3), t0, zero));
-                z[o + 2 * R] = cfma(__ldg(M + 8), t2, cfma(__ldg(M + 7), t1, cfma(__ldg(M + 6), t0, zero)));
-            }
+            __syncthreads();
         }
-        __syncthreads();
-    }
-    for (int lv = nlev - 1; lv >= 0; --lv) {
-        const int a = off[lv], n = (off[lv + 1] - a) * R;
-        for (int i = warp; i < n; i += kWarps) {
-            const int c = i % R;
-            if (!s_mask[c]) continue;
-            const int node = ord[a + i / R];
-            const size_t o = (size_t)3 * node * R + c;
-            double2 t0 = zero, t1 = zero, t2 = zero;
-            const int p = __ldg(P.rp + node) + lane;
-            if (p < __ldg(P.rp + node + 1)) {
-                const int J = __ldg(P.col + p);
-                if (J > node && J < r1) {
-                    const double2* L = P.bicp_l + (size_t)__ldg(P.bicp_tpos + p) * 9;  // block (J, I)
-                    const size_t oj = (size_t)3 * J * R + c;
-                    const double2 x0 = __ldcg(z + oj), x1 = __ldcg(z + oj + R), x2 = __ldcg(z + oj + 2 * R);
-                    t0 = cfma(__ldg(L + 6), x2, cfma(__ldg(L + 3), x1, cfma(__ldg(L + 0), x0, zero)));
-                    t1 = cfma(__ldg(L + 7), x2, cfma(__ldg(L + 4), x1, cfma(__ldg(L + 1), x0, zero)));
-                    t2 = cfma(__ldg(L + 8), x2, cfma(__ldg(L + 5), x1, cfma(__ldg(L + 2), x0, zero)));
-                }
-            }
-            t0 = warp_csum(t0);
-            t1 = warp_csum(t1);
-            t2 = warp_csum(t2);
-            if (lane == 0) {
-                const double2 y0 = __ldcg(z + o), y1 = __ldcg(z + o + R), y2 = __ldcg(z + o + 2 * R);
-                t0 = make_double2(y0.x - t0.x, y0.y - t0.y);
-                t1 = make_double2(y1.x - t1.x, y1.y - t1.y);
-                t2 = make_double2(y2.x - t2.x, y2.y - t2.y);
-                const double2* M = P.bicp_linv + (size_t)node * 9;  // z = M^T t, M lower triangular
-                z[o] = cfma(__ldg(M + 6), t2, cfma(__ldg(M + 3), t1, cfma(__ldg(M + 0), t0, zero)));
-                z[o + R] = cfma(__ldg(M + 7), t2, cfma(__ldg(M + 4), t1, zero));
-                z[o + 2 * R] = cfma(__ldg(M + 8), t2, zero);
-            }
-        }
-        __syncthreads();
     }
 }
 
@@ -764,7 +763,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     if (bicp) {
                         if (tid < R) s_bmask[tid] = s_repl[tid] && s_active[tid];
                         __syncthreads();
-                        bicp_apply<R>(P, cta, r0, r1, P.r, P.u, s_bmask);
+                        bicp_apply<R>(P, cta, r0, P.r, P.u, s_bmask);
                     }
                 }
             }
@@ -986,7 +985,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                 if (bicp) {
                     if (tid < R) s_bmask[tid] = s_active[tid] && !s_repl[tid];
                     __syncthreads();
-                    bicp_apply<R>(P, cta, r0, r1, P.r, P.u, s_bmask);
+                    bicp_apply<R>(P, cta, r0, P.r, P.u, s_bmask);
                 }
             }
         }
