@@ -410,7 +410,8 @@ def run_ours(args, rank, world, local_rank, precision_name):
 
 def run_spmv(args, rank, world, local_rank):
     """Standalone sparse products y = A x (fe_spmv) on the workload's matrix in
-    each precision, R = 1, 8 and 16 columns.  Algorithmic bytes per product
+    each precision, R = 1, 8 and 16 columns, and for complex64 and complex128
+    the same product from the half (lower-part) storage (fe_spmv_half).  Algorithmic bytes per product
     (s = bytes of one entry: complex64 8, complex128 and FP32 pairs 16):
     nnzb*(9*s + 4) + (n_nodes + 1)*4 + 2*n_dof*R*s.  Every timed product is
     preceded by a 512 MiB write that flushes L2 and is timed alone with CUDA
@@ -439,6 +440,7 @@ def run_spmv(args, rank, world, local_rank):
                                  ("df", fe.FE_PREC_DF, 16)):
             system = fe.fe_assemble(ctx, mesh, prob.freq_hz, prec)
             try:
+                kept = fe.fe_system_pack_half(ctx, system) if pname != "df" else 0  # storage #1 (Section 4.2)
                 for R in (1, 8, 16):
                     with torch.cuda.stream(stream):
                         if pname == "mixed":
@@ -450,27 +452,41 @@ def run_spmv(args, rank, world, local_rank):
                             x[..., 2:] *= 2.0 ** -24  # a valid low part
                         y = torch.empty_like(x)
                     stream.synchronize()
-                    for _ in range(max(3, args.warmup)):
-                        fe.fe_spmv(ctx, system, prec, R, x, y)
-                    times = []
-                    for _ in range(args.steps):
-                        with torch.cuda.stream(stream):
-                            flush.fill_(1)
-                            e0 = torch.cuda.Event(enable_timing=True)
-                            e1 = torch.cuda.Event(enable_timing=True)
-                            e0.record(stream)
-                        fe.fe_spmv(ctx, system, prec, R, x, y)
-                        with torch.cuda.stream(stream):
-                            e1.record(stream)
-                        stream.synchronize()
-                        times.append(e0.elapsed_time(e1))
-                        n_timed += 1
-                    ms = statistics.median(times)
+
+                    def timed(product):
+                        nonlocal n_timed
+                        for _ in range(max(3, args.warmup)):
+                            product(ctx, system, prec, R, x, y)
+                        times = []
+                        for _ in range(args.steps):
+                            with torch.cuda.stream(stream):
+                                flush.fill_(1)
+                                e0 = torch.cuda.Event(enable_timing=True)
+                                e1 = torch.cuda.Event(enable_timing=True)
+                                e0.record(stream)
+                            product(ctx, system, prec, R, x, y)
+                            with torch.cuda.stream(stream):
+                                e1.record(stream)
+                            stream.synchronize()
+                            times.append(e0.elapsed_time(e1))
+                            n_timed += 1
+                        return statistics.median(times)
+
+                    ms = timed(fe.fe_spmv)
                     by = nnzb * (9 * esz + 4) + (n + 1) * 4 + 2 * n_dof * R * esz
                     fl = (60 if pname == "df" else 8) * 9.0 * nnzb * R
                     table[f"{pname}_R{R}"] = {"ms": round(ms, 4), "gbs": round(by / ms / 1e6, 1),
                                              "frac_hbm": round(by / ms / 1e6 / hbm_peak, 4),
                                              "tflops": round(fl / ms / 1e9, 3), "bytes": int(by)}
+                    if kept:
+                        # half storage: kept blocks, every column index, the transposed
+                        # slot of each upper block, row pointers of both layouts, vectors
+                        ms_h = timed(fe.fe_spmv_half)
+                        by_h = kept * 9 * esz + nnzb * 4 + (nnzb - kept) * 4 + 2 * (n + 1) * 4 + 2 * n_dof * R * esz
+                        table[f"{pname}_half_R{R}"] = {
+                            "ms": round(ms_h, 4), "gbs": round(by_h / ms_h / 1e6, 1),
+                            "frac_hbm": round(by_h / ms_h / 1e6 / hbm_peak, 4), "bytes": int(by_h),
+                            "speedup_vs_full": round(ms / ms_h, 3)}
             finally:
                 fe.fe_system_destroy(system)
     fe.fe_mesh_destroy(mesh)

@@ -260,6 +260,26 @@ fe_status fe_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const fe_planewa
  * This is the sparse product at the heart of the Krylov loop (Section 3.1.5.1). */
 fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y);
 
+/* Half (symmetric) storage, storage #1 of Section 4.2: the symmetrised
+ * matrix kept by its lower part only.  fe_system_pack_half copies, per block
+ * row, the blocks (I, J <= I) of the system's complex128 values (and of its
+ * complex64 copy when it has one) into compacted planes, and indexes, for
+ * every block (I, J > I), the kept block (J, I) whose transpose it is.  The
+ * storage stays with the system (a new call replaces it) and costs about
+ * (14/27) of the values plus 4 bytes per block.  kept_blocks (optional)
+ * receives the number of kept blocks.  Errors: FE_ERR_INVALID_ARG (NULL,
+ * variant L, which is not symmetric, or no rows), FE_ERR_OOM, FE_ERR_CUDA. */
+fe_status fe_system_pack_half(fe_ctx* ctx, fe_system* s, int64_t* kept_blocks);
+
+/* y = A x from the half storage (the product of Section 4.2.5.1 on storage
+ * #1): an upper block is read as the transpose of the kept block of the
+ * neighbour's row.  precision FE_PREC_FP64 (complex128 vectors) or
+ * FE_PREC_MIXED (complex64 vectors; the system needs its complex64 copy).
+ * x, y: DEVICE buffers [n_dof][nrhs], nrhs a power of two <= 32; no
+ * aliasing.  Errors: FE_ERR_INVALID_ARG (NULL, nrhs, precision, no half
+ * storage), FE_ERR_CUDA. */
+fe_status fe_spmv_half(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nrhs, const void* x, void* y);
+
 /* ------------------------------------------------------------------------
  * Solve (Sections 3.1.5 and 4.2.5: conjugate gradients on the symmetric
  * system with diagonal preconditioning; here the complex-symmetric form,

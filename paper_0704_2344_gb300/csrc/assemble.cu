@@ -406,7 +406,12 @@ __global__ void k_row_cost(const signed char* __restrict__ cls, const StencilSet
     cost[r] = kind == 2 ? w_diagonal : (kind == 1 ? w_general : w_block * (row_ptr[r + 1] - row_ptr[r]));
 }
 
+// the half storage (half.cu) lives beside the system and goes with it
+void half_release(const fe_system* s);
+int64_t half_bytes(const fe_system* s);
+
 static void system_free(fe_system* s) {
+    half_release(s);
     cudaStream_t st = s->ctx->stream;
     for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
                       &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->bicp_l,
@@ -590,7 +595,7 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
                             &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->bicp_l,
                             &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         bytes += (int64_t)b->bytes;
-    out->device_bytes = bytes;
+    out->device_bytes = bytes + half_bytes(s);
     return FE_OK;
 }
 

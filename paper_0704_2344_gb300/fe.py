@@ -139,6 +139,8 @@ def load() -> C.CDLL:
         "fe_system_destroy": (None, [P]),
         "fe_rhs": (C.c_int, [P, P, C.c_int32, C.POINTER(fe_planewave), P, C.c_int32]),
         "fe_spmv": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P]),
+        "fe_system_pack_half": (C.c_int, [P, P, P]),
+        "fe_spmv_half": (C.c_int, [P, P, C.c_int32, C.c_int32, P, P]),
         "fe_solve_opts_default": (None, [C.POINTER(fe_solve_opts)]),
         "fe_solve_batch": (C.c_int, [P, P, C.c_int32, C.POINTER(fe_planewave), C.POINTER(fe_solve_opts), P,
                                      C.c_int32, C.POINTER(fe_solve_report)]),
@@ -377,6 +379,18 @@ def fe_rhs(ctx, system, waves, n_dof: int, out=None, on_device: bool = False):
 
 def fe_spmv(ctx, system, precision: int, nrhs: int, x, y):
     _check(load().fe_spmv(ctx, system, int(precision), int(nrhs), _ptr(x), _ptr(y)), "fe_spmv")
+
+
+def fe_system_pack_half(ctx, system) -> int:
+    """Builds the half (lower-part) storage of the system; returns the number
+    of kept blocks."""
+    n = C.c_int64(0)
+    _check(load().fe_system_pack_half(ctx, system, C.byref(n)), "fe_system_pack_half")
+    return int(n.value)
+
+
+def fe_spmv_half(ctx, system, precision: int, nrhs: int, x, y):
+    _check(load().fe_spmv_half(ctx, system, int(precision), int(nrhs), _ptr(x), _ptr(y)), "fe_spmv_half")
 
 
 def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
