@@ -265,9 +265,9 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
  * row, the blocks (I, J <= I) of the system's complex128 values (and of its
  * complex64 copy when it has one) into compacted planes, and indexes, for
  * every block (I, J > I), the kept block (J, I) whose transpose it is.  The
- * storage stays with the system (a new call replaces it) and costs about
- * (14/27) of the values plus 4 bytes per block.  kept_blocks (optional)
- * receives the number of kept blocks.  Errors: FE_ERR_INVALID_ARG (NULL,
+ * storage stays with the system (a new call replaces it), keeps a block's
+ * nine entries together, and costs about 14/27 of the values plus 4 bytes
+ * per block.  kept_blocks (optional) receives the number of kept blocks.  Errors: FE_ERR_INVALID_ARG (NULL,
  * variant L, which is not symmetric, or no rows), FE_ERR_OOM, FE_ERR_CUDA. */
 fe_status fe_system_pack_half(fe_ctx* ctx, fe_system* s, int64_t* kept_blocks);
 

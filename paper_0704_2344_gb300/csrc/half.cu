@@ -3,7 +3,8 @@
 //
 // The symmetrised matrix is kept by its lower part only: per block row the
 // blocks (I, J <= I), which are the row's first slots in the sorted block
-// pattern (diagonal last), compacted into 9 planes.  An upper block
+// pattern (diagonal last), compacted, the 9 entries of a block contiguous
+// (row-major 3x3).  An upper block
 // (I, J > I) is the transpose of the kept (J, I); a per-slot index gives
 // its place in row J.  The product is a gather: a warp per block row, a
 // lane per block of the full row, the upper lanes reading their block
@@ -11,7 +12,9 @@
 // about one grid plane of rows, while the neighbour's own warp has just
 // read the same block, so they are mostly served by L2, and the matrix
 // bytes read from HBM are about those of the kept half (14 of 27 blocks of
-// an interior row).
+// an interior row).  Keeping a block's entries together makes a
+// transposed read three 32-byte sectors (complex64) instead of one sector
+// per entry, as planes would.
 //
 // The storage belongs to a system: it is kept in a registry keyed by the
 // system and released with it.
@@ -26,11 +29,11 @@
 namespace fe {
 
 struct HalfStore {
-    int64_t nnzb = 0, stride = 0;  // kept blocks; plane stride (multiple of 64)
+    int64_t nnzb = 0;              // kept blocks
     DevBuf ptr;                    // int [n_act + 1]: first kept slot of each row
     DevBuf up;                     // int [nnzb]: kept slot of (J, I) for a full slot (I, J > I), else -1
-    DevBuf val64;                  // double2 [9 * stride]
-    DevBuf val32;                  // float2 [9 * stride] (systems with a complex64 copy)
+    DevBuf val64;                  // double2 [nnzb][9], row-major 3x3 per block
+    DevBuf val32;                  // float2 [nnzb][9] (systems with a complex64 copy)
     cudaStream_t st = nullptr;
 };
 
@@ -62,7 +65,7 @@ __global__ void k_half_count(int n, const int* __restrict__ rp, const int* __res
 // (J, I) among row J's kept blocks.
 template <typename C>
 __global__ void k_half_fill(int n, const int* __restrict__ rp, const int* __restrict__ col, const int* __restrict__ hp,
-                            const C* __restrict__ val, int64_t stride, C* __restrict__ hval, int64_t hstride,
+                            const C* __restrict__ val, int64_t stride, C* __restrict__ hval,
                             int* __restrict__ up, int* __restrict__ status) {
     const int I = blockIdx.x * blockDim.x + threadIdx.x;
     if (I >= n) return;
@@ -72,7 +75,7 @@ __global__ void k_half_fill(int n, const int* __restrict__ rp, const int* __rest
         if (J <= I) {
             const int q = q0 + (p - p0);
 #pragma unroll
-            for (int k = 0; k < 9; ++k) hval[k * hstride + q] = val[k * stride + p];
+            for (int k = 0; k < 9; ++k) hval[(size_t)q * 9 + k] = val[k * stride + p];
             if (up) up[p] = -1;
         } else if (up) {
             int t = -1;
@@ -89,8 +92,7 @@ __global__ void k_half_fill(int n, const int* __restrict__ rp, const int* __rest
 // full-storage product), a block read directly for J <= I and transposed
 // from row J for J > I; the groups' partial sums meet in a fixed butterfly.
 template <typename C, int R>
-__global__ void __launch_bounds__(256) k_spmv_half(const C* __restrict__ hval, int64_t hstride,
-                                                   const int* __restrict__ hp, const int* __restrict__ up,
+__global__ void __launch_bounds__(256) k_spmv_half(const C* __restrict__ hval, const int* __restrict__ hp, const int* __restrict__ up,
                                                    const int* __restrict__ col, const int* __restrict__ rp,
                                                    const C* __restrict__ x, C* __restrict__ y, int n_rows) {
     using Tr = decltype(C{}.x);
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(256) k_spmv_half(const C* __restrict__ hval, i
             const int cb = __ldg(col + s);
             C m[9];
 #pragma unroll
-            for (int k = 0; k < 9; ++k) m[k] = __ldg(hval + k * hstride + q);
+            for (int k = 0; k < 9; ++k) m[k] = __ldg(hval + (size_t)q * 9 + k);
             const int xb = 3 * cb * R + c;
             C xv[3];
 #pragma unroll
@@ -133,15 +135,15 @@ __global__ void __launch_bounds__(256) k_spmv_half(const C* __restrict__ hval, i
 }
 
 template <typename C>
-void launch_half(int R, unsigned blocks, cudaStream_t st, const C* hval, int64_t hstride, const int* hp, const int* up,
+void launch_half(int R, unsigned blocks, cudaStream_t st, const C* hval, const int* hp, const int* up,
                  const int* col, const int* rp, const C* x, C* y, int n) {
     switch (R) {
-        case 1: k_spmv_half<C, 1><<<blocks, 256, 0, st>>>(hval, hstride, hp, up, col, rp, x, y, n); break;
-        case 2: k_spmv_half<C, 2><<<blocks, 256, 0, st>>>(hval, hstride, hp, up, col, rp, x, y, n); break;
-        case 4: k_spmv_half<C, 4><<<blocks, 256, 0, st>>>(hval, hstride, hp, up, col, rp, x, y, n); break;
-        case 8: k_spmv_half<C, 8><<<blocks, 256, 0, st>>>(hval, hstride, hp, up, col, rp, x, y, n); break;
-        case 16: k_spmv_half<C, 16><<<blocks, 256, 0, st>>>(hval, hstride, hp, up, col, rp, x, y, n); break;
-        default: k_spmv_half<C, 32><<<blocks, 256, 0, st>>>(hval, hstride, hp, up, col, rp, x, y, n); break;
+        case 1: k_spmv_half<C, 1><<<blocks, 256, 0, st>>>(hval, hp, up, col, rp, x, y, n); break;
+        case 2: k_spmv_half<C, 2><<<blocks, 256, 0, st>>>(hval, hp, up, col, rp, x, y, n); break;
+        case 4: k_spmv_half<C, 4><<<blocks, 256, 0, st>>>(hval, hp, up, col, rp, x, y, n); break;
+        case 8: k_spmv_half<C, 8><<<blocks, 256, 0, st>>>(hval, hp, up, col, rp, x, y, n); break;
+        case 16: k_spmv_half<C, 16><<<blocks, 256, 0, st>>>(hval, hp, up, col, rp, x, y, n); break;
+        default: k_spmv_half<C, 32><<<blocks, 256, 0, st>>>(hval, hp, up, col, rp, x, y, n); break;
     }
 }
 
@@ -222,17 +224,16 @@ fe_status fe_system_pack_half(fe_ctx* ctx, fe_system* s, int64_t* kept_blocks) {
         return fail(FE_ERR_CUDA);
     }
     h->nnzb = total;
-    h->stride = ((int64_t)total + 63) / 64 * 64;
-    if ((e = dev_alloc(st, h->val64, (size_t)h->stride * 9 * sizeof(double2))) != FE_OK) return fail(e);
+    if ((e = dev_alloc(st, h->val64, (size_t)total * 9 * sizeof(double2))) != FE_OK) return fail(e);
     k_half_fill<double2><<<blocks_for_n(n, 128), 128, 0, st>>>(n, rp, col, hp, (const double2*)s->val64.ptr,
-                                                               s->stride, (double2*)h->val64.ptr, h->stride,
-                                                               (int*)h->up.ptr, (int*)status.ptr);
+                                                               s->stride, (double2*)h->val64.ptr, (int*)h->up.ptr,
+                                                               (int*)status.ptr);
     count_launches(1);
     if (s->val32.ptr) {
-        if ((e = dev_alloc(st, h->val32, (size_t)h->stride * 9 * sizeof(float2))) != FE_OK) return fail(e);
+        if ((e = dev_alloc(st, h->val32, (size_t)total * 9 * sizeof(float2))) != FE_OK) return fail(e);
         k_half_fill<float2><<<blocks_for_n(n, 128), 128, 0, st>>>(n, rp, col, hp, (const float2*)s->val32.ptr,
-                                                                 s->stride, (float2*)h->val32.ptr, h->stride,
-                                                                 nullptr, (int*)status.ptr);
+                                                                 s->stride, (float2*)h->val32.ptr, nullptr,
+                                                                 (int*)status.ptr);
         count_launches(1);
     }
     int hs = 0;
@@ -274,14 +275,14 @@ fe_status fe_spmv_half(fe_ctx* ctx, const fe_system* s, int32_t precision, int32
     const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)ctx->num_sms * 8,
                                                                              ((int64_t)m->n_act + 7) / 8));
     if (precision == FE_PREC_FP64) {
-        launch_half<double2>(nrhs, blocks, st, (const double2*)h->val64.ptr, h->stride, (const int*)h->ptr.ptr,
+        launch_half<double2>(nrhs, blocks, st, (const double2*)h->val64.ptr, (const int*)h->ptr.ptr,
                              (const int*)h->up.ptr, col, rp, (const double2*)x, (double2*)y, m->n_act);
     } else if (precision == FE_PREC_MIXED) {
         if (!h->val32.ptr) {
             set_error("fe_spmv_half: no complex64 copy (system assembled in FP64)");
             return FE_ERR_INVALID_ARG;
         }
-        launch_half<float2>(nrhs, blocks, st, (const float2*)h->val32.ptr, h->stride, (const int*)h->ptr.ptr,
+        launch_half<float2>(nrhs, blocks, st, (const float2*)h->val32.ptr, (const int*)h->ptr.ptr,
                             (const int*)h->up.ptr, col, rp, (const float2*)x, (float2*)y, m->n_act);
     } else {
         set_error("fe_spmv_half: precision must be FE_PREC_FP64 or FE_PREC_MIXED");
