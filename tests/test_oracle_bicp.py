@@ -125,3 +125,24 @@ def test_bicp_cocg_reaches_the_direct_solution(n_sub):
     xref = fem.solve_direct(A, b)
     assert np.linalg.norm(x - xref) <= 1e-7 * np.linalg.norm(xref)
     assert 0 < it < 400
+
+
+def test_held_unknowns_stay_unit_rows_and_columns():
+    """Symmetry planes hold unknowns as identity rows and columns of A
+    (Eqs. 6a/6b).  Eq. 5 then gives L_ii = 1 and no coupling to or from a
+    held unknown, exactly, and L L^T = A still holds on the pattern."""
+    prob = W.empty_box((6, 6, 4), name="bicp_planes")
+    prob.material[1:3, 2:4, 2:4] = PEC
+    part = W.mirror_part(prob, 2, 1)
+    maps = fem.mesh_maps(part)
+    held = np.asarray(maps.fixed)
+    assert held.any()
+    A = fem.assemble(part, maps=maps)
+    for n_sub in (1, 5):
+        L = precond.ic0(A, maps, n_sub).toarray()
+        assert np.all(L[held, held] == 1)
+        L0 = L.copy()
+        L0[held, held] = 0
+        assert np.all(L0[held, :] == 0) and np.all(L0[:, held] == 0)
+        mask = _pattern_mask(maps, n_sub)
+        assert np.abs((L @ L.T - A.toarray())[mask]).max() <= 1e-13 * np.abs(A.data).max()
