@@ -224,7 +224,8 @@ fe_status fe_system_export_df(fe_ctx* ctx, const fe_system* s, void* vals_df);
  * The factor is FP64 and is used by FE_PREC_FP64 solves.  It is built on the
  * device (one thread per band) and kept with the system (16 B x 9 per stored
  * block, plus index arrays); a new call replaces it.
- * Errors: FE_ERR_INVALID_ARG (NULL, no rows, n_sub outside [0, n]),
+ * Errors: FE_ERR_INVALID_ARG (NULL, no rows, variant L, which is not
+ * symmetric, n_sub outside [0, n]),
  * FE_ERR_BREAKDOWN (a pivot is zero or not finite; no factor is kept),
  * FE_ERR_OOM, FE_ERR_CUDA. */
 fe_status fe_system_factor_bicp(fe_ctx* ctx, fe_system* s, int32_t n_sub);

@@ -232,8 +232,8 @@ fe_status fe_system_factor_bicp(fe_ctx* ctx, fe_system* s, int32_t n_sub) {
         return FE_ERR_INVALID_ARG;
     }
     const fe_mesh* m = s->mesh;
-    if (!s->val64.ptr || m->n_act < 1) {
-        set_error("fe_system_factor_bicp: the system has no FP64 values or no rows");
+    if (!s->val64.ptr || m->n_act < 1 || s->variant == FE_VARIANT_L) {
+        set_error("fe_system_factor_bicp: needs a symmetric variant (S or P) with rows");
         return FE_ERR_INVALID_ARG;
     }
     const int n = m->n_act;

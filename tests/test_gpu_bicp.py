@@ -154,3 +154,21 @@ def test_bicp_argument_errors(fe, ctx):
     finally:
         fe.fe_system_destroy(s)
         fe.fe_mesh_destroy(m)
+
+
+def test_bicp_rejects_the_unsymmetric_variant(fe):
+    """Variant L (literal Eq. 4) is not symmetric: no incomplete Cholesky factor."""
+    c = fe.fe_ctx_create(0, variant=fe.FE_VARIANT_L)
+    try:
+        prob = W.random_small_grid(4, n_max=6)
+        m = fe.fe_mesh_create_from(c, prob)
+        s = fe.fe_assemble(c, m, prob.freq_hz, fe.FE_PREC_FP64)
+        try:
+            with pytest.raises(fe.FeError) as e:
+                fe.fe_system_factor_bicp(c, s, 0)
+            assert e.value.status == fe.FE_ERR_INVALID_ARG
+        finally:
+            fe.fe_system_destroy(s)
+            fe.fe_mesh_destroy(m)
+    finally:
+        fe.fe_ctx_destroy(c)
