@@ -190,6 +190,28 @@ def algorithmic_flops(info, sysinfo, precision_name, inner_iters, passes, R=1):
     return inner_iters * product, inner_iters * vec64 + passes * outer64
 
 
+def method_products(reports, tile):
+    """Sparse products one step's persistent launches perform, from the
+    per-column reports: a launch of `tile` columns runs as many inner
+    iterations as its slowest column (one product each), one FP64
+    true-residual product per refinement pass (`outer`), and one more inner
+    product after every intermediate refinement (s = A p is recomputed)."""
+    inner = fp64 = 0
+    for t0 in range(0, len(reports), tile):
+        cols = reports[t0:t0 + tile]
+        outer = max(r["outer"] for r in cols)
+        inner += max(r["iterations"] for r in cols) + max(outer - 2, 0)
+        fp64 += outer
+    return inner, fp64
+
+
+def product_bytes(info, s, R):
+    """The method's bytes for one block-sparse product with R columns
+    (entries of s bytes): every stored block (9 entries and a 4-byte column
+    index), the row pointers, and the input and output vectors."""
+    return info["nnzb"] * (9 * s + 4) + (info["n_nodes"] + 1) * 4 + 2 * info["n_dof"] * s * R
+
+
 # ALU peaks from the unit counts and clock: 152 SMs x 128 FP32 lanes x 2 flops
 # x 2.07 GHz; FP64 issues at 1/64 of the FP32 rate on GB300.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # 80.5 (an FMA loop on the box measured 72)
@@ -304,6 +326,8 @@ def run_ours(args, rank, world, local_rank, precision_name):
     evs = []
     kernel_ms = 0.0
     inner_iters = passes = 0
+    prod_inner = prod_fp64 = 0
+    tile_w = 1
     statuses = []
     t_wall0 = time.perf_counter()
     with ClockSampler(local_rank) as clk:
@@ -319,6 +343,10 @@ def run_ours(args, rank, world, local_rank, precision_name):
             inner_iters += stats["inner_iters"]
             passes += stats["passes"]
             statuses.append((st, [r["rel_residual"] for r in rep], [r["iterations"] for r in rep]))
+            tile_w = max(1, int(stats.get("tile_width") or 1))
+            ni, nf = method_products(rep, tile_w)
+            prod_inner += ni
+            prod_fp64 += nf
         torch.cuda.synchronize()
     replicas.barrier()
     torch.cuda.synchronize()
@@ -347,40 +375,53 @@ def run_ours(args, rank, world, local_rank, precision_name):
     peaks = json.loads((ROOT / "MEASURED_PEAKS.json").read_text()) if (ROOT / "MEASURED_PEAKS.json").exists() else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_src = "measured" if "hbm_gbs" in peaks else "fallback"
-    secs = kernel_ms * 1e-3
-    hbm_view = {"achieved_gbs": round(alg / secs / 1e9, 1), "peak_gbs": hbm_peak,
-                "frac": round(alg / secs / 1e9 / hbm_peak, 4)} if secs > 0 else None
-    common = {"algorithmic_bytes_per_launch": int(alg / args.steps),
+    common = {"implementation_bytes_per_launch": int(alg / args.steps),
               "product_flops_per_launch": int(fl_prod / args.steps), "fp64_flops_per_launch": int(fl64 / args.steps),
               "product_rows": dict(zip(("blocks_explicit", "rows_general", "rows_diagonal"),
                                        product_rows(sysinfo, base)))}
     if bicp:
         common["bicp_band_blocks"] = bicp_blocks
         common["bicp_factor_ms"] = round(bicp_factor_ms, 3)
+    # The roofline of the method's own work (the survey's per-product bytes
+    # and flops), not of the arithmetic that implements it.
+    s_inner = 8 if base == "mixed" else 16
+    steps = args.steps
+    pb_inner = product_bytes(info, s_inner, tile_w)
+    pb_fp64 = product_bytes(info, 16, tile_w)
+    method_bytes = (prod_inner * pb_inner + prod_fp64 * pb_fp64) / steps
+    method_flops = (prod_inner + prod_fp64) * info["nnzb"] * 72.0 * tile_w / steps
+    work = {"bytes_per_product": pb_inner, "bytes_per_fp64_product": pb_fp64,
+            "products_per_launch": prod_inner / steps, "fp64_products_per_launch": prod_fp64 / steps,
+            "method_bytes_per_launch": int(method_bytes), "method_flops_per_launch": int(method_flops),
+            "entry_bytes": s_inner, "columns_per_launch": tile_w}
+    launch_s = launch_ms * 1e-3
     if base == "fp64":
-        # the complex128 products run on the FP64 pipes (1/64 of the FP32 rate on GB300): ALU-bound
-        achieved = (fl_prod + fl64) / secs / 1e12 if secs > 0 else None
-        roof = {"kernel": f"k_solve<double,{R}> (persistent COCG, FP64"
+        # complex128 products run on the FP64 pipes (1/64 of the FP32 rate):
+        # 8 flops per complex multiply-add against that rate
+        achieved = method_flops / launch_s / 1e12 if launch_s > 0 else None
+        roof = {"kernel": f"k_solve<double,{tile_w}> (persistent COCG, FP64"
                           + (", block incomplete Cholesky)" if bicp else ")"), "bound": "alu",
                 "achieved": round(achieved, 4) if achieved else None, "peak": round(FP64_PEAK_TFLOPS, 3),
                 "unit": "TFLOP/s", "frac": round(achieved / FP64_PEAK_TFLOPS, 4) if achieved else None,
-                "peak_source": "FP64 rate from unit counts and clock (1.20 measured)", "hbm_view": hbm_view}
-    elif base == "df":
-        # FP32-pair products on the FP32 pipes; the FP64 vector work issues
-        # at 1/64 of that rate, so it is counted as 64 FP32-equivalent flops
-        achieved = (fl_prod + 64.0 * fl64) / secs / 1e12 if secs > 0 else None
-        roof = {"kernel": f"k_solve<DFloat,{R}> (persistent COCG, FP32-pair products)", "bound": "alu",
-                "achieved": round(achieved, 3) if achieved else None, "peak": round(FP32_PEAK_TFLOPS, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / FP32_PEAK_TFLOPS, 4) if achieved else None,
-                "peak_source": "FP32 rate from unit counts and clock (FMA loop measured 72)",
-                "flops_note": "FP32-pair product flops plus 64 x the FP64 vector flops", "hbm_view": hbm_view}
+                "peak_source": "FP64 rate from unit counts and clock (an FMA loop measured 1.20)",
+                "work": "method_flops_per_launch / (launch_ms * 1e-3) / 1e12",
+                "hbm_view": {"achieved_gbs": round(method_bytes / launch_s / 1e9, 1), "peak_gbs": hbm_peak,
+                             "frac": round(method_bytes / launch_s / 1e9 / hbm_peak, 4)} if launch_s > 0 else None}
     else:
-        achieved = alg / secs / 1e9 if secs > 0 else None
-        roof = {"kernel": f"k_solve<float,{R}> (persistent COCG, complex64 products)", "bound": "hbm",
+        achieved = method_bytes / launch_s / 1e9 if launch_s > 0 else None
+        roof = {"kernel": f"k_solve<{'DFloat' if base == 'df' else 'float'},{tile_w}> (persistent COCG, "
+                          + ("FP32-pair" if base == "df" else "complex64") + " products)", "bound": "hbm",
                 "achieved": round(achieved, 1) if achieved else None, "peak": hbm_peak, "unit": "GB/s",
-                "frac": round(achieved / hbm_peak, 4) if achieved else None, "peak_source": hbm_src}
+                "frac": round(achieved / hbm_peak, 4) if achieved else None,
+                "peak_source": f"{hbm_src} (MEASURED_PEAKS.json hbm_gbs)" if hbm_src == "measured" else hbm_src,
+                "work": "(products_per_launch * bytes_per_product + fp64_products_per_launch * "
+                        "bytes_per_fp64_product) / (launch_ms * 1e-3) / 1e9",
+                "alu_view": {"method_tflops": round(method_flops / launch_s / 1e12, 3) if launch_s > 0 else None,
+                             "fp32_peak_tflops": round(FP32_PEAK_TFLOPS, 2)}}
+    roof.update(work)
+    roof["stencil_reduced_bytes_per_launch"] = int(alg / steps)   # what the class-stencil product actually reads
     roof.update(common)
-    roof["traffic"] = recorded_traffic(args.workload, precision_name)
+    roof["traffic"] = recorded_traffic(args.workload, precision_name)   # ncu DRAM bytes per launch (or None)
     roof["launch_ms"] = round(launch_ms, 4)
     roof["kernel_share_of_step"] = round(kernel_ms / total_ms, 4) if total_ms else None
     fe.fe_ctx_destroy(ctx)

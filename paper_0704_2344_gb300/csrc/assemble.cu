@@ -414,7 +414,7 @@ static void system_free(fe_system* s) {
     half_release(s);
     cudaStream_t st = s->ctx->stream;
     for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
-                      &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->bicp_l,
+                      &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix, &s->bicp_l,
                       &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         dev_free(st, *b);
     s->bicp_n_sub = 0;
@@ -535,10 +535,12 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         // row: a general-stencil row costs 18 (complex64) or 31 (FP32 pairs)
         // such blocks, a diagonal-stencil row 10 or 8 (per-CTA product times
         // measured on GB300 and fitted to these three row kinds)
-        const int weights[2][3] = {{1, 18, 10}, {1, 31, 8}};
-        DevBuf* bufs[2] = {&s->cost_prefix, &s->cost_prefix_alu};
+        // The third prefix counts the stored blocks of explicit rows only: a
+        // solve CTA packs its explicit rows' values at 9 times that prefix.
+        const int weights[3][3] = {{1, 18, 10}, {1, 31, 8}, {1, 0, 0}};
+        DevBuf* bufs[3] = {&s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix};
         int* d_total = (int*)ctx->small.ptr + 24;
-        for (int k = 0; k < 2; ++k) {
+        for (int k = 0; k < 3; ++k) {
             if ((e = dev_alloc(st, *bufs[k], (size_t)(m->n_act + 1) * sizeof(int))) != FE_OK) return fail(e);
             int* cp = (int*)bufs[k]->ptr;
             k_row_cost<<<(unsigned)((m->n_act + 255) / 256), 256, 0, st>>>(
@@ -592,7 +594,7 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
     out->blocks_explicit = s->blocks_explicit;
     int64_t bytes = 0;
     for (const DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
-                            &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->bicp_l,
+                            &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix, &s->bicp_l,
                             &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         bytes += (int64_t)b->bytes;
     out->device_bytes = bytes + half_bytes(s);

@@ -176,6 +176,8 @@ struct fe_system {
     // the same with the weights of the FP32-pair products
     fe::DevBuf cost_prefix_alu;      // int [n_act + 1]
     int64_t cost_total_alu = 0;
+    // prefix sum of the stored blocks of explicit rows (rows of no class)
+    fe::DevBuf expl_prefix;          // int [n_act + 1]; expl_prefix[n_act] = blocks_explicit
     int cost_min[2] = {1, 1}, cost_max[2] = {1, 1};  // bounds of one row's cost (complex64, FP32 pairs)
     int64_t rows_general = 0, rows_diagonal = 0, blocks_explicit = 0;  // rows per product path
     // Block incomplete Cholesky factor (Section 3.1.5.3): node rows split into

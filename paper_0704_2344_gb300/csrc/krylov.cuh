@@ -240,18 +240,19 @@ namespace fe {
 // (row, alpha) walks the row's blocks; per block it reads the column index,
 // the three entries (alpha, 0..2) from their planes and the three vector
 // entries at the column.  No cross-lane reduction is needed.  `xs` is
-// indexed by vector entry minus `xoff`.
-template <typename C, bool kShared>
+// indexed by vector entry minus `xoff`.  cols[s - s0] is the block's column
+// (node) index, or with kElem the index in `xs` of the column's first vector
+// entry (a column map resolved once per launch).
+template <typename C, bool kShared, bool kElem = false>
 __device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t stride, const int* cols, int s0, int s1,
                                            int al, const C* xs, int xoff) {
-    // cols: the row's column indices in shared memory, cols[s - s0]
   if constexpr (std::is_same<C, float4>::value) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     const float4* v0 = val + (3 * al) * stride;
     const float4* v1 = v0 + stride;
     const float4* v2 = v1 + stride;
     for (int s = s0; s < s1; ++s) {
-        const int xa = 3 * cols[s - s0] - xoff;
+        const int xa = (kElem ? cols[s - s0] : 3 * cols[s - s0]) - xoff;
         const float4 m0 = ld_ro(v0 + s), m1 = ld_ro(v1 + s), m2 = ld_ro(v2 + s);
         const float4 x0 = kShared ? xs[xa] : ld_cg(xs + xa), x1 = kShared ? xs[xa + 1] : ld_cg(xs + xa + 1),
                      x2 = kShared ? xs[xa + 2] : ld_cg(xs + xa + 2);
@@ -268,7 +269,8 @@ __device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t st
     const C* v2 = v1 + stride;
     int s = s0;
     for (; s + 1 < s1; s += 2) {  // two blocks per step, two accumulator pairs
-        const int xa = 3 * cols[s - s0] - xoff, xb = 3 * cols[s + 1 - s0] - xoff;
+        const int xa = (kElem ? cols[s - s0] : 3 * cols[s - s0]) - xoff,
+                  xb = (kElem ? cols[s + 1 - s0] : 3 * cols[s + 1 - s0]) - xoff;
         const C ma0 = ld_ro(v0 + s), ma1 = ld_ro(v1 + s), ma2 = ld_ro(v2 + s);
         const C mb0 = ld_ro(v0 + s + 1), mb1 = ld_ro(v1 + s + 1), mb2 = ld_ro(v2 + s + 1);
         const C xa0 = kShared ? xs[xa] : ld_cg(xs + xa), xa1 = kShared ? xs[xa + 1] : ld_cg(xs + xa + 1),
@@ -281,7 +283,7 @@ __device__ __forceinline__ C row_component(const C* __restrict__ val, int64_t st
         bi += mb0.x * xb0.y + mb0.y * xb0.x + mb1.x * xb1.y + mb1.y * xb1.x + mb2.x * xb2.y + mb2.y * xb2.x;
     }
     if (s < s1) {
-        const int xa = 3 * cols[s - s0] - xoff;
+        const int xa = (kElem ? cols[s - s0] : 3 * cols[s - s0]) - xoff;
         const C m0 = ld_ro(v0 + s), m1 = ld_ro(v1 + s), m2 = ld_ro(v2 + s);
         const C x0 = kShared ? xs[xa] : ld_cg(xs + xa), x1 = kShared ? xs[xa + 1] : ld_cg(xs + xa + 1),
                 x2 = kShared ? xs[xa + 2] : ld_cg(xs + xa + 2);
@@ -381,7 +383,7 @@ __device__ __forceinline__ int stage_cols(const int* __restrict__ rp, const int*
 // Component alpha of a regular row (all 27 blocks present) from the class
 // stencil: a real diagonal stencil (kind 2) needs one vector entry and one
 // real multiply-add per block; general blocks (kind 1) a full 3x3 product.
-template <typename C, bool kShared>
+template <typename C, bool kShared, bool kElem = false>
 __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ S, int cls, int kind, const int* cols,
                                                  int al, const C* xs, int xoff) {
   if constexpr (std::is_same<C, float4>::value) {
@@ -390,7 +392,7 @@ __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ 
         const float2* d = S->dvaldf[cls][al];
 #pragma unroll 9
         for (int kk = 0; kk < 27; ++kk) {
-            const int xi = 3 * cols[kk] + al - xoff;
+            const int xi = (kElem ? cols[kk] : 3 * cols[kk]) + al - xoff;
             const float4 xv = kShared ? xs[xi] : ld_cg(xs + xi);
             const float2 dk = __ldg(d + kk);
             df_mac(acc[0], acc[1], dk.x, dk.y, xv.x, xv.z);
@@ -400,7 +402,7 @@ __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ 
         const float4* sp = S->sdf[cls][al][0];
 #pragma unroll 3
         for (int kk = 0; kk < 27; ++kk) {
-            const int xi = 3 * cols[kk] - xoff;
+            const int xi = (kElem ? cols[kk] : 3 * cols[kk]) - xoff;
 #pragma unroll
             for (int be = 0; be < 3; ++be) dfc_mac(acc, ld_ro(sp + 3 * kk + be), kShared ? xs[xi + be] : ld_cg(xs + xi + be));
         }
@@ -414,7 +416,7 @@ __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ 
         const Tr* d = kF32 ? (const Tr*)S->dval32[cls][al] : (const Tr*)S->dval[cls][al];
 #pragma unroll 9
         for (int kk = 0; kk < 27; ++kk) {
-            const int xi = 3 * cols[kk] + al - xoff;
+            const int xi = (kElem ? cols[kk] : 3 * cols[kk]) + al - xoff;
             const C xv = kShared ? xs[xi] : ld_cg(xs + xi);
             const Tr dk = __ldg(d + kk);
             ar += dk * xv.x;
@@ -424,7 +426,7 @@ __device__ __forceinline__ C row_component_class(const StencilSet* __restrict__ 
         const C* s = kF32 ? (const C*)S->s32[cls][al][0] : (const C*)S->s64[cls][al][0];
 #pragma unroll 3
         for (int kk = 0; kk < 27; ++kk) {
-            const int xi = 3 * cols[kk] - xoff;
+            const int xi = (kElem ? cols[kk] : 3 * cols[kk]) - xoff;
 #pragma unroll
             for (int be = 0; be < 3; ++be) {
                 const C m = ld_ro(s + 3 * kk + be);

@@ -32,7 +32,7 @@ int64_t job_rows(const SolveJob* j);
 void job_destroy(fe_ctx* ctx, SolveJob* j);
 fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n);
 fe_status job_collect(fe_ctx* ctx, SolveJob* j, fe_complex* x_host, fe_solve_report* rep);
-size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta);
+size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta, int64_t pk_entries);
 fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewave* waves, double2* d_B,
                     DevBuf& wave_buf);
 
@@ -83,7 +83,9 @@ int64_t estimate_bytes(const fe_mesh_desc& d, int nrhs, int width, int prec, int
     const int64_t per_entry = prec == FE_PREC_FP64 ? 16 : (prec == FE_PREC_MIXED ? 24 : 32);
     const int64_t sys = 9 * stride * per_entry + 9 * nodes * 24 + nodes * 13 + 65536;
     const int64_t rhs = 3 * nodes * (int64_t)nrhs * 16;
-    const int64_t ws = (int64_t)workspace_bytes(3 * nodes, width, prec, num_sms);
+    // the packed explicit rows of a single-column launch: at most every block
+    const int64_t pk = (width == 1 && prec != FE_PREC_FP64) ? 9 * nnzb : 0;
+    const int64_t ws = (int64_t)workspace_bytes(3 * nodes, width, prec, 2 * num_sms, pk);
     return (mesh + sys + rhs + ws) * 11 / 10 + (1 << 20);
 }
 

@@ -62,7 +62,7 @@ static int pick_tile(int nrhs, int requested) {
 
 static void free_workspace(cudaStream_t st, Workspace& w) {
     for (DevBuf* b : {&w.b, &w.x, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.pM, &w.w, &w.partial, &w.result, &w.sync, &w.rep,
-                      &w.trace})
+                      &w.trace, &w.pk})
         dev_free(st, *b);
 }
 
@@ -73,7 +73,10 @@ static size_t inner_bytes(int prec) { return prec == FE_PREC_MIXED ? sizeof(floa
 
 // Whether the products read separate inner-precision copies of u and p
 // (complex64; FP32 pairs with one column) instead of the vectors themselves.
-static bool split_copies(int prec, int R) { return prec == FE_PREC_MIXED || (prec == FE_PREC_DF && R == 1); }
+static bool split_copies(int prec, int R) {
+    (void)R;
+    return prec == FE_PREC_MIXED;
+}
 
 // Inner-precision matrix planes of a system, or NULL when it was not
 // assembled for that precision.
@@ -101,7 +104,15 @@ static fe_status with_inner_type(int prec, F&& f) {
     }
 }
 
-static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec, int max_cta, Workspace& w) {
+// Entries of the packed explicit rows a single-column complex64 or
+// FP32-pair launch copies its explicit rows into (0: none).
+static int64_t packed_entries(const fe_system* s, int prec, int R) {
+    if (R != 1 || prec == FE_PREC_FP64 || !s->expl_prefix.ptr) return 0;
+    return 9 * s->blocks_explicit;
+}
+
+static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec, int max_cta, Workspace& w,
+                                 int64_t pk_entries = 0) {
     const size_t esz = inner_bytes(prec);  // inner-precision vectors (uM, w)
     const size_t nv = (size_t)n_dof * R;
     for (auto pr : {std::make_pair(&w.b, nv * sizeof(double2)), std::make_pair(&w.x, nv * sizeof(double2)),
@@ -119,15 +130,22 @@ static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec
             return e;
         }
     }
+    if (pk_entries > 0) {
+        const fe_status e = dev_alloc(st, w.pk, (size_t)pk_entries * inner_bytes(prec));
+        if (e != FE_OK) {
+            free_workspace(st, w);
+            return e;
+        }
+    }
     return FE_OK;
 }
 
 // Bytes alloc_workspace takes (before allocator rounding).
-size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta) {
+size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta, int64_t pk_entries) {
     const size_t nv = (size_t)n_dof * R;
     const size_t esz = inner_bytes(prec);
     return nv * (6 * sizeof(double2) + (split_copies(prec, R) ? 3 : 1) * esz) + (size_t)(max_cta + 1) * kMaxNV * R * sizeof(double) +
-           (size_t)R * 32 + 4096;
+           (size_t)R * 32 + 4096 + (size_t)pk_entries * esz;
 }
 
 // Solve parameters for a tile of R columns held in workspace w (n_cta and the
@@ -162,16 +180,19 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.u = (double2*)w.u.ptr;
     P.p = (double2*)w.p.ptr;
     P.s = (double2*)w.s.ptr;
-    // FP64 vectors, and FP32-pair vectors (FE_PREC_DF with R > 1), feed the
+    // FP64 vectors, and the FP32-pair vectors of FE_PREC_DF, feed the
     // products directly
-    const bool direct = fp64 || (df && R > 1);
+    const bool direct = fp64 || df;
     P.uM = direct ? w.u.ptr : w.uM.ptr;
     P.pM = direct ? w.p.ptr : w.pM.ptr;
     P.w = w.w.ptr;
     P.trace = (unsigned long long*)w.trace.ptr;
+    P.pk = classes ? w.pk.ptr : nullptr;
+    P.expl_prefix = classes ? (const int*)s->expl_prefix.ptr : nullptr;
     // lexicographic node ranks: a neighbour is at most one plane, one line
     // and one node away
     P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
+    P.res_tmid = (m->nx + 1) + 1;  // same-plane neighbours: one line and one node away
     P.sync = (SyncState*)w.sync.ptr;
     P.partial = (double*)w.partial.ptr;
     P.result = (double*)w.result.ptr;
@@ -213,7 +234,7 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
     FE_TRY(check_precond(ctx, s, o, "solve"));
     Workspace w;
     auto cleanup = [&]() { free_workspace(st, w); };
-    fe_status e = alloc_workspace(st, n_dof, R, prec, 2 * ctx->num_sms, w);
+    fe_status e = alloc_workspace(st, n_dof, R, prec, 2 * ctx->num_sms, w, packed_entries(s, prec, R));
     if (e != FE_OK) return e;
     const bool tracing = getenv("FE_TRACE") && getenv("FE_TRACE")[0] == '1';
     const size_t trace_bytes =
@@ -344,7 +365,7 @@ fe_status job_create(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d
     j->prec = prec;
     j->n_dof = 3 * (int64_t)s->mesh->n_act;
     cudaStream_t st = ctx->stream;
-    fe_status e = alloc_workspace(st, j->n_dof, j->R, prec, ctx->num_sms, j->w);
+    fe_status e = alloc_workspace(st, j->n_dof, j->R, prec, 2 * ctx->num_sms, j->w, packed_entries(s, prec, j->R));
     if (e != FE_OK) {
         delete j;
         return e;

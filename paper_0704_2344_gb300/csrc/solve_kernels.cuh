@@ -19,6 +19,7 @@ constexpr int kWarps = kThreads / 32;
 constexpr int kMaxNV = 11;    // reduced values per column and barrier
 constexpr int kTraceIters = 64;
 constexpr int kRowsPerWarpR1 = 10;   // R = 1 products: one thread per (row, component), 10 rows per warp
+constexpr int kExplRows = 10;        // packed explicit rows: ten rows per warp, one lane per (row, component)
 constexpr int kColsPerWarp = 272;    // >= 10 rows x 27 blocks
 constexpr int kTracePhases = 8;
 
@@ -71,8 +72,26 @@ struct SolveParams {
     int halo;       // bound on |column rank - row rank|
     int stage;      // stage the CTA's uM halo in shared memory (1) or gather from L2 (0)
     int64_t halo_bytes;  // dynamic shared memory left for the halo (a CTA whose halo is larger gathers)
+    int64_t part_half;   // doubles per parity buffer of the barrier partials (n_cta * kMaxNV * R)
     int red_bytes;  // dynamic shared memory used by the column sums
     int col_bytes;  // dynamic shared memory for the per-warp column-index staging (R = 1)
+    // Resident product map (R = 1, complex64 and FP32-pair products): each
+    // CTA sorts its product rows by cost once per launch and keeps them, their
+    // block ranges and their columns resolved to positions in its staged halo
+    // in shared memory; the halo is staged as up to three segments (the node
+    // planes below, at and above the CTA's rows) instead of one window.
+    int res;           // 1: the map is in use
+    int res_rows_max;  // rows the map holds (a CTA with more rows uses the plain path)
+    int res_tmid;      // |column - row| bound of same-plane neighbours (the middle segment)
+    int res_bytes;     // dynamic shared memory of the map (a multiple of 16)
+    // Packed explicit rows (with the map): each launch, every CTA copies the
+    // values of its explicit rows into this buffer in the order its lanes read
+    // them, so that each product step of a warp loads 30 consecutive entries
+    // per block column instead of one scattered entry per lane; a CTA's part
+    // starts at 9 * expl_prefix[first product row].  NULL: the lanes read the
+    // planes.
+    void* pk;                 // inner-precision entries [9 * explicit blocks]
+    const int* expl_prefix;   // [n_rows + 1] stored blocks of explicit rows before each row
     int* rep_status;
     int* rep_iters;
     int* rep_outer;
@@ -91,65 +110,105 @@ struct SolveParams {
 };
 
 // ---------------------------------------------------------------------------
-// Grid barrier with fused reduction.  Every CTA writes NV partial values and
-// arrives on a counter; the last arrival sums the partials of all CTAs in CTA
-// order (lane-strided, then a fixed butterfly), publishes the NV results and
-// bumps the generation.  One thread per CTA fences: the CTA barrier before
-// it makes the whole CTA's writes part of its release (fences are
-// cumulative).  Waits are bounded by P.timeout_ns; on expiry the CTA records
-// kDevTimeout and every CTA leaves at its next barrier.
+// Grid barrier with fused reduction.  Every CTA writes NV partial values,
+// then one thread per CTA fences and arrives on a counter that only grows
+// within a launch (barrier e of the launch completes when it reaches
+// (e + 1) * n_cta).  After the wait, every CTA sums the partials of all CTAs
+// itself, in CTA order (lane-strided, then a fixed butterfly), so all CTAs
+// obtain bitwise the same results without a second round trip through a
+// CTA that reduces and publishes.  Partials alternate between two buffers
+// by barrier parity: a CTA can only write barrier e + 2's partials after
+// every CTA has arrived at barrier e + 1, that is after every CTA has read
+// barrier e's.  The CTA barrier before the fence makes the whole CTA's
+// writes part of its release (fences are cumulative).  Waits are bounded by
+// P.timeout_ns; on expiry the CTA records kDevTimeout and every CTA leaves
+// at its next barrier.
 // ---------------------------------------------------------------------------
-template <int NV>
+static __shared__ unsigned g_bar_epoch;  // barriers this CTA has passed in this launch
+
+// Arrival with release semantics at GPU scope (orders the CTA's earlier
+// writes, which the preceding CTA barrier made this thread's, before it) and
+// the matching acquire load of the counter.
+__device__ __forceinline__ void arrive_release(unsigned* count) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(count), "r"(1u) : "memory");
+}
+__device__ __forceinline__ unsigned load_acquire(const unsigned* count) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void grid_barrier_init() {
+    if (threadIdx.x == 0) g_bar_epoch = 0u;
+}
+
+// kPair: the partials travel and are summed as FP32 pairs (hi = RN32(v),
+// lo = RN32(v - hi); TwoSum additions), on the FP32 pipes.  On this GPU a
+// warp's FP64 instruction holds the SM's FP64 pipe for about 16 cycles, so
+// sums that every CTA repeats are kept off it.
+template <int NV, bool kPair = false>
 __device__ __noinline__ bool grid_reduce(const SolveParams& P, int cta, const double* s_in, double* s_out) {
-    __shared__ int s_last, s_ok;
+    __shared__ int s_ok;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int v = threadIdx.x; v < NV; v += kThreads) P.partial[(size_t)cta * NV + v] = s_in[v];
+    const unsigned ep = g_bar_epoch;
+    double* part = P.partial + (size_t)(ep & 1u) * (size_t)P.part_half;
+    for (int v = threadIdx.x; v < NV; v += kThreads) {
+        if (kPair) {
+            const float hi = __double2float_rn(s_in[v]);
+            ((float2*)part)[(size_t)cta * NV + v] = make_float2(hi, __double2float_rn(s_in[v] - (double)hi));
+        } else {
+            part[(size_t)cta * NV + v] = s_in[v];
+        }
+    }
     __syncthreads();
-    volatile unsigned* vgen = &P.sync->gen;
-    volatile int* verr = &P.sync->err;
     if (threadIdx.x == 0) {
-        const unsigned g = *vgen;
-        __threadfence();
-        const unsigned old = atomicAdd(&P.sync->count, 1u);
-        s_ok = 1;
-        s_last = old == (unsigned)P.n_cta - 1u;
-        if (!s_last) {
+        volatile int* verr = &P.sync->err;
+        arrive_release(&P.sync->count);
+        const unsigned target = (ep + 1u) * (unsigned)P.n_cta;
+        int ok = 1;
+        if ((int)(load_acquire(&P.sync->count) - target) < 0) {
             const unsigned long long t0 = globaltimer_ns();
-            while (*vgen == g) {
+            while ((int)(load_acquire(&P.sync->count) - target) < 0) {
                 if (*verr) {
-                    s_ok = 0;
+                    ok = 0;
                     break;
                 }
                 if (globaltimer_ns() - t0 > P.timeout_ns) {
                     atomicCAS(&P.sync->err, 0, kDevTimeout);
-                    s_ok = 0;
+                    ok = 0;
                     break;
                 }
                 if (P.spin_ns) __nanosleep(P.spin_ns);
             }
         }
-        __threadfence();
+        s_ok = ok && *verr == 0;
+        g_bar_epoch = ep + 1u;
     }
     __syncthreads();
-    if (s_last) {
+    if (NV > 0 && s_ok) {
         for (int v = warp; v < NV; v += kWarps) {
-            double acc = 0.0;
-            for (int c = lane; c < P.n_cta; c += 32) acc += __ldcg(P.partial + (size_t)c * NV + v);
+            if (kPair) {
+                float h = 0.f, l = 0.f;
+                for (int c = lane; c < P.n_cta; c += 32) {
+                    const float2 q = __ldcg((const float2*)part + (size_t)c * NV + v);
+                    df_add(h, l, q.x, q.y);
+                }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) P.result[v] = acc;
+                for (int o = 16; o > 0; o >>= 1) {
+                    const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+                    df_add(h, l, h2, l2);
+                }
+                if (lane == 0) s_out[v] = (double)h + (double)l;
+            } else {
+                double acc = 0.0;
+                for (int c = lane; c < P.n_cta; c += 32) acc += __ldcg(part + (size_t)c * NV + v);
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                if (lane == 0) s_out[v] = acc;
+            }
         }
         __syncthreads();
-        if (threadIdx.x == 0) {
-            __threadfence();
-            atomicExch(&P.sync->count, 0u);
-            __threadfence();
-            atomicAdd(&P.sync->gen, 1u);
-        }
     }
-    if (threadIdx.x == 0 && *verr) s_ok = 0;
-    for (int v = threadIdx.x; v < NV; v += kThreads) s_out[v] = __ldcg(P.result + v);
-    __syncthreads();
     return s_ok != 0;
 }
 
@@ -173,6 +232,37 @@ __device__ __forceinline__ void cta_colsum(const double (&v)[NV], double* s_red,
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
         if (lane == 0) s_in[i] = acc;
+    }
+    __syncthreads();
+}
+
+// The same for FP32-pair values (f[2k] + f[2k + 1] is value k), with TwoSum
+// additions; only the NV * R CTA totals are converted to FP64.
+template <int R, int NV>
+__device__ __forceinline__ void cta_colsum_df(const float (&f)[2 * NV], double* s_red, double* s_in) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float2* s_redf = (float2*)s_red;
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+        float h = f[2 * k], l = f[2 * k + 1];
+#pragma unroll
+        for (int o = 16; o >= R; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            df_add(h, l, h2, l2);
+        }
+        if (lane < R) s_redf[(k * kWarps + warp) * R + lane] = make_float2(h, l);
+    }
+    __syncthreads();
+    for (int i = warp; i < NV * R; i += kWarps) {
+        const int k = i / R, c = i % R;
+        const float2 q = s_redf[(k * kWarps + lane) * R + c];  // kWarps == 32
+        float h = q.x, l = q.y;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
+            df_add(h, l, h2, l2);
+        }
+        if (lane == 0) s_in[i] = (double)h + (double)l;
     }
     __syncthreads();
 }
@@ -252,6 +342,262 @@ __device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int
     return ok;
 }
 
+// ---------------------------------------------------------------------------
+// Resident product map of an R = 1 launch.  Products cost very different
+// amounts per row (an explicit row walks up to 27 stored 3x3 blocks, a
+// diagonal-stencil row 27 real weights), and a warp lasts as long as its
+// slowest lane; rows are therefore sorted by cost (explicit rows by block
+// count, then general-stencil rows, then diagonal-stencil rows) so that a
+// warp's ten rows cost alike, and the costly row groups spread over the
+// CTA's warps and the SM's four schedulers.  The sort, the block ranges and
+// the column map are built once per launch.  The halo of the product input
+// is staged as up to three byte ranges (lexicographic node ranks put a
+// row's neighbours one plane below, in its own plane and one plane above),
+// which for the voxel grids here is about a third of the single window
+// from the lowest to the highest neighbour.
+// ---------------------------------------------------------------------------
+struct ResMap {
+    int n;                 // rows of the CTA's product range
+    int nslot;             // sorted slots: explicit rows, padding to a multiple of 10, class rows
+    int nexpl;             // explicit slots including their padding (row -1)
+    long long pk_base;     // first entry of the CTA's packed explicit rows
+    int staged;            // the segments fit the halo buffer
+    int nseg;              // byte ranges staged per product
+    unsigned total;        // their total bytes
+    long long a0[3];       // first global byte of each range (16-byte aligned)
+    unsigned bytes[3];     // its length (a multiple of 16)
+    unsigned soff[3];      // its offset in the halo buffer
+    int lo[3], hi[3];      // the node (column) range it covers
+};
+
+template <typename C>
+__device__ __noinline__ void build_res_map(const SolveParams& P, int pr0, int pr1, int* rows, int2* meta, int* cols,
+                                           int* goff, ResMap& rm) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int n = pr1 - pr0;
+    int* keys = cols;  // scratch until the column map is written
+    __shared__ int s_lo[3], s_hi[3];
+    for (int i = tid; i < n; i += kThreads) {
+        const int row = pr0 + i;
+        const int cls = P.row_class ? P.row_class[row] : -1;
+        const int kind = cls >= 0 ? P.stencil->kind[cls] : 0;
+        const int nb = P.rp[row + 1] - P.rp[row];
+        keys[i] = kind == 2 ? 21 : (kind == 1 ? 20 : max(0, min(19, 27 - nb)));
+    }
+    if (tid < 3) {
+        s_lo[tid] = 0x7fffffff;
+        s_hi[tid] = -1;
+    }
+    __syncthreads();
+    // stable counting sort by key (one warp; deterministic); the explicit
+    // rows are padded with empty slots (row -1) to a multiple of kExplRows,
+    // so that every warp group holds rows of one kind
+    if (warp == 0) {
+        int base = 0;
+        for (int b = 0; b < 22; ++b) {
+            if (b == 20) {
+                const int pad = (base + kExplRows - 1) / kExplRows * kExplRows;
+                for (int i = base + lane; i < pad; i += 32) rows[i] = -1;
+                if (lane == 0) rm.nexpl = pad;
+                base = pad;
+            }
+            for (int c0 = 0; c0 < n; c0 += 32) {
+                const int i = c0 + lane;
+                const bool m = i < n && keys[i] == b;
+                const unsigned bal = __ballot_sync(0xffffffffu, m);
+                if (m) rows[base + __popc(bal & ((1u << lane) - 1u))] = pr0 + i;
+                base += __popc(bal);
+            }
+        }
+        if (lane == 0) rm.nslot = base;
+    }
+    __syncthreads();
+    const int nslot = rm.nslot;
+    // block ranges; column bounds of the three neighbour groups
+    for (int i = warp; i < nslot; i += kWarps) {
+        const int row = rows[i];
+        if (row < 0) {
+            if (lane == 0) meta[i] = make_int2(0, 0);
+            continue;
+        }
+        const int s0 = __ldg(P.rp + row), nb = __ldg(P.rp + row + 1) - s0;
+        if (lane == 0) {
+            const int cls = P.row_class ? P.row_class[row] : -1;
+            const int kind = cls >= 0 ? P.stencil->kind[cls] : 0;
+            meta[i] = make_int2(s0, nb | (kind << 8) | ((cls & 0xff) << 16));
+        }
+        if (lane < nb) {
+            const int c = __ldg(P.col + s0 + lane);
+            const int d = c - row;
+            const int g = d < -P.res_tmid ? 0 : (d > P.res_tmid ? 2 : 1);
+            atomicMin(&s_lo[g], c);
+            atomicMax(&s_hi[g], c);
+        }
+    }
+    __syncthreads();
+    if (tid == 0) {
+        // packed explicit rows: offsets of the warp groups (entries)
+        int acc = 0;
+        for (int g = 0; g * kExplRows < rm.nexpl; ++g) {
+            goff[g] = acc;
+            for (int j = 0; j < kExplRows; ++j) acc += 9 * (meta[g * kExplRows + j].y & 0xff);
+        }
+        rm.pk_base = P.expl_prefix ? 9ll * P.expl_prefix[pr0] : 0ll;
+        // non-empty ranges in ascending order, merged where they overlap or
+        // nearly touch
+        int lo[3], hi[3], m = 0;
+        for (int g = 0; g < 3; ++g)
+            if (s_hi[g] >= 0) {
+                lo[m] = s_lo[g];
+                hi[m] = s_hi[g];
+                ++m;
+            }
+        for (int a = 0; a < m; ++a)
+            for (int b = a + 1; b < m; ++b)
+                if (lo[b] < lo[a]) {
+                    const int tl = lo[a], th = hi[a];
+                    lo[a] = lo[b];
+                    hi[a] = hi[b];
+                    lo[b] = tl;
+                    hi[b] = th;
+                }
+        int k = 0;
+        for (int a = 0; a < m; ++a) {
+            if (k > 0 && lo[a] <= rm.hi[k - 1] + 8) {
+                rm.hi[k - 1] = max(rm.hi[k - 1], hi[a]);
+            } else {
+                rm.lo[k] = lo[a];
+                rm.hi[k] = hi[a];
+                ++k;
+            }
+        }
+        unsigned off = 0;
+        for (int a = 0; a < k; ++a) {
+            const long long b0 = 3ll * rm.lo[a] * (long long)sizeof(C), b1 = 3ll * (rm.hi[a] + 1) * (long long)sizeof(C);
+            const long long a0 = b0 & ~15ll, a1 = (b1 + 15) & ~15ll;
+            rm.a0[a] = a0;
+            rm.bytes[a] = (unsigned)(a1 - a0);
+            rm.soff[a] = off;
+            off += (unsigned)(a1 - a0);
+        }
+        rm.nseg = k;
+        rm.total = off;
+        rm.n = n;
+        rm.staged = (P.stage && k > 0 && (long long)off <= P.halo_bytes) ? 1 : 0;
+    }
+    __syncthreads();
+    // column map: the position of the column's first vector entry in the
+    // halo buffer (staged) or in the global vector
+    for (int i = warp; i < nslot; i += kWarps) {
+        const int2 mt = meta[i];
+        const int nb = mt.y & 0xff;
+        if (lane < nb) {
+            const int c = __ldg(P.col + mt.x + lane);
+            int e = 3 * c;
+            if (rm.staged) {
+                int a = 0;
+                while (a + 1 < rm.nseg && c > rm.hi[a]) ++a;
+                e = (int)(((long long)rm.soff[a] + 3ll * c * (long long)sizeof(C) - rm.a0[a]) / (long long)sizeof(C));
+            }
+            cols[i * 27 + lane] = e;
+        }
+    }
+    __syncthreads();
+}
+
+// Packs the values of the CTA's explicit rows for the product: in warp group
+// g (kExplRows slots, rows sorted by block count, most first), step k takes
+// the k-th block of the J_k rows that have one, stored as
+// [beta][row j][alpha], so that entry (alpha, beta) of row j sits at
+// beta * 3 J_k + 3j + alpha.  No entry is padding.  Values come from the
+// planes (read-only); the product phase reads them back in the same launch
+// through L2.
+template <typename C>
+__device__ __noinline__ void pack_explicit(const SolveParams& P, const int* rows, const int2* meta, const int* goff,
+                                           const ResMap& rm) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const C* valM = (const C*)P.valM;
+    C* pk = (C*)P.pk + rm.pk_base;
+    const int j = lane / 3, al = lane % 3;
+    for (int g = warp; g * kExplRows < rm.nexpl; g += kWarps) {
+        const int slot = g * kExplRows + j;
+        const bool valid = lane < 3 * kExplRows && rows[slot] >= 0;
+        const int2 mt = valid ? meta[slot] : make_int2(0, 0);
+        const int nb = mt.y & 0xff;
+        const int K = __shfl_sync(0xffffffffu, nb, 0);
+        C* pg = pk + goff[g];
+        int off = 0;
+        for (int k = 0; k < K; ++k) {
+            const int Jk = __popc(__ballot_sync(0xffffffffu, al == 0 && valid && k < nb));
+            if (k < nb) {
+#pragma unroll
+                for (int be = 0; be < 3; ++be)
+                    pg[off + be * 3 * Jk + 3 * j + al] = ld_ro(valM + (3 * al + be) * P.stride + mt.x + k);
+            }
+            off += 9 * Jk;
+        }
+    }
+}
+
+// Stages the map's byte ranges of v into the halo buffer with bulk (TMA)
+// copies on one mbarrier.  Returns false when the bounded wait expired.
+__device__ __forceinline__ bool stage_res(const SolveParams& P, const void* v, const ResMap& rm, char* halo_buf,
+                                          uint64_t* mbar, unsigned& phase) {
+    if (threadIdx.x == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(mbar, rm.total);
+        for (int a = 0; a < rm.nseg; ++a) bulk_g2s(halo_buf + rm.soff[a], (const char*)v + rm.a0[a], rm.bytes[a], mbar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns)) != 0;
+    if (!ok) {
+        atomicCAS(&P.sync->err, 0, kDevTimeout);
+        mbar_wait_bounded(mbar, phase & 1u, P.timeout_ns > 2000000000ull ? P.timeout_ns : 2000000000ull);
+    }
+    phase += 1;
+    return ok;
+}
+
+// Views of the resident map in shared memory.
+struct ResView {
+    const int* rows;
+    const int2* meta;
+    const int* cols;
+    const int* goff;  // packed entries before each explicit warp group
+    const float2* dvw;  // diagonal-stencil weights [class][alpha][27] in shared memory (FP32 pair, or .x alone)
+    const ResMap* rm;
+};
+
+// Component alpha of a diagonal-stencil row (27 real weights, shared
+// memory) times the vector; cols holds element indices.
+template <typename C, bool kShared>
+__device__ __forceinline__ C row_component_diag(const float2* dv, const int* cols, int al, const C* xs) {
+    const float2* d = dv + al * 27;
+  if constexpr (std::is_same<C, float4>::value) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 9
+    for (int kk = 0; kk < 27; ++kk) {
+        const int xi = cols[kk] + al;
+        const float4 xv = kShared ? xs[xi] : ld_cg(xs + xi);
+        const float2 dk = d[kk];
+        df_mac(acc[0], acc[1], dk.x, dk.y, xv.x, xv.z);
+        df_mac(acc[2], acc[3], dk.x, dk.y, xv.y, xv.w);
+    }
+    return df_result(acc);
+  } else {
+    using Tr = decltype(C{}.x);
+    Tr ar = 0, ai = 0;
+#pragma unroll 9
+    for (int kk = 0; kk < 27; ++kk) {
+        const int xi = cols[kk] + al;
+        const C xv = kShared ? xs[xi] : ld_cg(xs + xi);
+        const Tr dk = (Tr)d[kk].x;
+        ar += dk * xv.x;
+        ai += dk * xv.y;
+    }
+    return mk(ar, ai);
+  }
+}
+
 // One Krylov product phase over the CTA's rows: w = A uM and, for columns
 // whose s must be refreshed after a residual replacement, s = A pM; with the
 // per-column FP64 partial dots
@@ -262,12 +608,11 @@ __device__ __forceinline__ bool stage_halo(const SolveParams& P, const C* v, int
 template <typename TM, int R, bool kStaged, int NV>
 __device__ __forceinline__ bool product_phase(const SolveParams& P, const typename CplxT<TM>::type* xs, int xshift,
                                               int r0, int r1, const int* s_refresh, bool any_refresh, int* s_cols,
-                                              double (&acc)[NV]) {
+                                              double (&acc)[NV], float (&facc)[2 * NV], const ResView* rv) {
     constexpr bool kRefresh = NV == 11;
-    // FP32-pair vectors: dots accumulate as FP32 pairs, facc[2k] + facc[2k+1]
-    // is acc[k] (converted to FP64 once, at the end of the phase)
-    constexpr bool kDFV = std::is_same<TM, DFloat>::value && (R > 1);
-    float facc[kDFV ? 2 * NV : 1] = {};
+    // FP32-pair vectors: dots accumulate as FP32 pairs in facc (facc[2k] +
+    // facc[2k+1] is dot k), summed over the CTA as pairs as well
+    constexpr bool kDFV = std::is_same<TM, DFloat>::value;
     bool ok = true;
     using C = typename CplxT<TM>::type;
     const C* valM = (const C*)P.valM;
@@ -312,7 +657,105 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
         }
       }
     };
-    if (R == 1) {
+    if (R == 1 && kClassPath<C> && rv != nullptr) {
+        // resident map: ten rows of like cost per warp (sorted slots); row
+        // groups go to warps in snake order, so a warp that takes two groups
+        // pairs a costly one with a cheap one
+        const bool refresh = kRefresh && s_refresh[0] != 0;
+        const int al = lane % 3;
+        const int n = rv->rm->nslot;
+        const int nexpl = rv->rm->nexpl;
+        const int n_eg = nexpl / kExplRows;  // explicit groups (kExplRows rows), then class groups (ten rows)
+        const int n_groups = n_eg + (n - nexpl + kRowsPerWarpR1 - 1) / kRowsPerWarpR1;
+        const bool packed = P.pk != nullptr;
+        for (int k = 0; k * kWarps < n_groups; ++k) {
+            const int g = k * kWarps + ((k & 1) ? kWarps - 1 - warp : warp);
+            if (g >= n_groups) continue;
+            if (g < n_eg && packed) {
+                // explicit rows from the packed copy: lane 3j + alpha walks the
+                // blocks of row j, component alpha; each step loads 3 J_k
+                // consecutive entries per block column
+                const int j = lane / 3;
+                const int slot = g * kExplRows + j;
+                const bool valid = lane < 3 * kExplRows && rv->rows[slot] >= 0;
+                const int2 mt = valid ? rv->meta[slot] : make_int2(0, 0);
+                const int nb = mt.y & 0xff;
+                const int K = __shfl_sync(0xffffffffu, nb, 0);
+                const C* pg = (const C*)P.pk + rv->rm->pk_base + rv->goff[g];
+                const int* rc = rv->cols + slot * 27;
+                const C* xv = kStaged ? xs : uM;
+                const bool lead = al == 0 && valid;  // one lane per row counts the rows of a step
+                int off = 0;
+                C y;
+                if constexpr (std::is_same<C, float4>::value) {
+                    float a4[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int kk = 0; kk < K; ++kk) {
+                        const int Jk = __popc(__ballot_sync(0xffffffffu, lead && kk < nb));
+                        if (kk < nb) {
+                            const int e = rc[kk];
+                            const C* pe = pg + off + 3 * j + al;
+                            const C m0 = ld_cg(pe), m1 = ld_cg(pe + 3 * Jk), m2 = ld_cg(pe + 6 * Jk);
+                            const C x0 = kStaged ? xv[e] : ld_cg(xv + e), x1 = kStaged ? xv[e + 1] : ld_cg(xv + e + 1),
+                                    x2 = kStaged ? xv[e + 2] : ld_cg(xv + e + 2);
+                            dfc_mac(a4, m0, x0);
+                            dfc_mac(a4, m1, x1);
+                            dfc_mac(a4, m2, x2);
+                        }
+                        off += 9 * Jk;
+                    }
+                    y = df_result(a4);
+                } else {
+                    using Tr = decltype(C{}.x);
+                    Tr ar = 0, ai = 0;
+                    for (int kk = 0; kk < K; ++kk) {
+                        const int Jk = __popc(__ballot_sync(0xffffffffu, lead && kk < nb));
+                        if (kk < nb) {
+                            const int e = rc[kk];
+                            const C* pe = pg + off + 3 * j + al;
+                            const C m0 = ld_cg(pe), m1 = ld_cg(pe + 3 * Jk), m2 = ld_cg(pe + 6 * Jk);
+                            const C x0 = kStaged ? xv[e] : ld_cg(xv + e), x1 = kStaged ? xv[e + 1] : ld_cg(xv + e + 1),
+                                    x2 = kStaged ? xv[e + 2] : ld_cg(xv + e + 2);
+                            ar += m0.x * x0.x - m0.y * x0.y + m1.x * x1.x - m1.y * x1.y + m2.x * x2.x - m2.y * x2.y;
+                            ai += m0.x * x0.y + m0.y * x0.x + m1.x * x1.y + m1.y * x1.x + m2.x * x2.y + m2.y * x2.x;
+                        }
+                        off += 9 * Jk;
+                    }
+                    y = mk(ar, ai);
+                }
+                if (valid) {
+                    const int row = rv->rows[slot];
+                    const size_t o = (size_t)3 * row + al;
+                    w[o] = y;
+                    C sy = y;
+                    if (refresh) sy = row_component<C, false>(valM, P.stride, P.col + mt.x, mt.x, mt.x + nb, al, pM, 0);
+                    dots(o, y, refresh, sy);
+                }
+                continue;
+            }
+            // class rows (ten per warp), or explicit rows read from the planes
+            // when no packed copy exists (kExplRows per warp)
+            const int slot = g < n_eg ? g * kExplRows + lane / 3 : nexpl + (g - n_eg) * kRowsPerWarpR1 + lane / 3;
+            const int lanes = g < n_eg ? 3 * kExplRows : 3 * kRowsPerWarpR1;
+            if (lane < lanes && slot < n && rv->rows[slot] >= 0) {
+                const int2 mt = rv->meta[slot];
+                const int row = rv->rows[slot];
+                const int s0 = mt.x, s1 = mt.x + (mt.y & 0xff);
+                const int kind = (mt.y >> 8) & 0xff;
+                const int cls = (int)(signed char)((mt.y >> 16) & 0xff);
+                const int* rc = rv->cols + slot * 27;
+                const C y = kind == 2 ? row_component_diag<C, kStaged>(rv->dvw + cls * 81, rc, al, kStaged ? xs : uM)
+                            : kind ? row_component_class<C, kStaged, true>(P.stencil, cls, kind, rc, al, kStaged ? xs : uM, 0)
+                                   : row_component<C, kStaged, true>(valM, P.stride, rc, s0, s1, al, kStaged ? xs : uM, 0);
+                const size_t o = (size_t)3 * row + al;
+                w[o] = y;
+                C sy = y;
+                if (refresh)
+                    sy = kind ? row_component_class<C, false>(P.stencil, cls, kind, P.col + s0, al, pM, 0)
+                              : row_component<C, false>(valM, P.stride, P.col + s0, s0, s1, al, pM, 0);
+                dots(o, y, refresh, sy);
+            }
+        }
+    } else if (R == 1) {
         // one thread per (row, component): ten rows per warp, their column
         // indices staged in shared memory first
         int* cols = s_cols + warp * kColsPerWarp;
@@ -370,10 +813,6 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
                 dots(o, y[al], refresh, refresh ? sy[al] : y[al]);
             }
         }
-    }
-    if constexpr (kDFV) {
-#pragma unroll
-        for (int k = 0; k < NV; ++k) acc[k] += (double)facc[2 * k] + (double)facc[2 * k + 1];
     }
     (void)any_refresh;
     return ok;
@@ -498,18 +937,30 @@ template <typename TM, int R, int NV>
 __device__ __forceinline__ bool product_step(const SolveParams& P, int cta, bool stage_fits,
                                              const typename CplxT<TM>::type* uM, int pr0, int pr1, char* halo_buf,
                                              uint64_t* mbar, unsigned& mbar_phase, const int* s_refresh,
-                                             bool any_refresh, int* s_cols, double (&acc)[NV], int trace_it) {
+                                             bool any_refresh, int* s_cols, double (&acc)[NV],
+                                             float (&facc)[2 * NV], int trace_it, const ResView* rv) {
     using C = typename CplxT<TM>::type;
     const int tid = threadIdx.x;
     bool ok;
-    if (stage_fits) {
+    if (rv != nullptr) {
+        if (rv->rm->staged) {
+            if (!stage_res(P, uM, *rv->rm, halo_buf, mbar, mbar_phase)) return false;
+            FE_TRACE_MARK(1);
+            ok = product_phase<TM, R, true, NV>(P, (const C*)halo_buf, 0, pr0, pr1, s_refresh, any_refresh, s_cols,
+                                                acc, facc, rv);
+        } else {
+            ok = product_phase<TM, R, false, NV>(P, nullptr, 0, pr0, pr1, s_refresh, any_refresh, s_cols, acc, facc,
+                                                 rv);
+        }
+    } else if (stage_fits) {
         int shift = 0;
         if (!stage_halo<C, R>(P, uM, pr0, pr1, halo_buf, mbar, mbar_phase, shift)) return false;
         FE_TRACE_MARK(1);
         ok = product_phase<TM, R, true, NV>(P, (const C*)halo_buf, shift, pr0, pr1, s_refresh, any_refresh, s_cols,
-                                            acc);
+                                            acc, facc, nullptr);
     } else {
-        ok = product_phase<TM, R, false, NV>(P, nullptr, 0, pr0, pr1, s_refresh, any_refresh, s_cols, acc);
+        ok = product_phase<TM, R, false, NV>(P, nullptr, 0, pr0, pr1, s_refresh, any_refresh, s_cols, acc, facc,
+                                             nullptr);
     }
     if (!ok && tid == 0) atomicCAS(&P.sync->err, 0, kDevTimeout);
     return ok;
@@ -530,11 +981,12 @@ __device__ __forceinline__ bool product_step(const SolveParams& P, int cta, bool
 template <typename TM, int R>
 __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) {
     using C = typename CplxT<TM>::type;
-    // Krylov vectors: FP64, or FP32 pairs in the FE_PREC_DF mode with several
-    // columns (then the products read u and p directly and the updates run
-    // on the FP32 pipes; with one column the FP64 recurrences converge in
-    // fewer iterations and the update is cheap either way)
-    constexpr bool kDFV = std::is_same<TM, DFloat>::value && (R > 1);
+    // Krylov vectors: FP64, or FP32 pairs in the FE_PREC_DF mode (then the
+    // products read u and p directly, and the updates, dots and reductions
+    // run on the FP32 pipes: a warp's FP64 instruction holds the SM's FP64
+    // pipe for about 16 cycles on this GPU, so FP64 vector work that every
+    // thread repeats costs microseconds per iteration)
+    constexpr bool kDFV = std::is_same<TM, DFloat>::value;
     using VT = std::conditional_t<kDFV, float4, double2>;
     VT* X = (VT*)P.x;
     VT* Rv = (VT*)P.r;
@@ -551,12 +1003,18 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
 
     extern __shared__ __align__(128) char dyn[];
     double* s_red = (double*)dyn;
-    int* s_cols = (int*)(dyn + P.red_bytes);
-    char* halo_buf = dyn + P.red_bytes + P.col_bytes;
+    // shared memory: [column sums][column staging][halo], or with the
+    // resident map [column sums][map][halo], where the true-residual phase
+    // stages its column indices at the start of the halo buffer (no bulk copy
+    // is in flight outside the product phases)
+    char* halo_buf = dyn + P.red_bytes + P.col_bytes + P.res_bytes;
+    int* s_cols = P.res ? (int*)halo_buf : (int*)(dyn + P.red_bytes);
     __shared__ __align__(8) uint64_t s_mbar;
     __shared__ double s_in[kMaxNV * R], s_out[kMaxNV * R];
     __shared__ double s_bn[R], s_rr_ref[R], s_rel[R];
     __shared__ double s_gam_r[R], s_gam_i[R], s_al_r[R], s_al_i[R], s_be_r[R], s_be_i[R];
+    __shared__ double s_igam_r[R], s_igam_i[R], s_ial_r[R], s_ial_i[R];  // 1/gamma, 1/alpha of the last iteration
+    __shared__ float4 s_a4[R], s_na4[R], s_b4[R];  // alpha, -alpha, beta as FP32 pairs (FP32-pair updates)
     __shared__ int s_bmask[R];  // columns a block incomplete Cholesky application writes
     __shared__ int s_active[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_first[R], s_refresh[R],
         s_repl[R], s_pass_it[R];
@@ -603,12 +1061,40 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         st[5] = nd;
     }
     // stage the product input only if this CTA's halo fits the buffer
-    const bool stage_fits = P.stage && [&] {
+    const bool stage_fits = P.stage && !P.res && [&] {
         const int h0 = max(0, pr0 - P.halo), h1 = min(P.n_rows, pr1 + P.halo);
         const size_t a0 = ((size_t)3 * h0 * R * sizeof(C)) & ~(size_t)15;
         const size_t a1 = ((size_t)3 * h1 * R * sizeof(C) + 15) & ~(size_t)15;
         return a1 - a0 <= (size_t)P.halo_bytes;
     }();
+    // resident product map (R = 1 class-path products, when the host sized it)
+    constexpr bool kRes = kClassPath<TM> && R == 1;
+    __shared__ ResMap s_rm;
+    __shared__ float2 s_dvw[kRes ? kMaxClasses * 81 : 1];
+    ResView rv_local{nullptr, nullptr, nullptr, nullptr, s_dvw, &s_rm};
+    const ResView* rv = nullptr;
+    if constexpr (kRes) {
+        if (P.res && pr1 - pr0 + kRowsPerWarpR1 <= P.res_rows_max) {
+            int* rrows = (int*)(dyn + P.red_bytes);
+            int2* rmeta = (int2*)(rrows + P.res_rows_max);
+            int* rcols = (int*)(rmeta + P.res_rows_max);
+            int* rgoff = rcols + 27 * P.res_rows_max;
+            for (int i = tid; i < kMaxClasses * 81; i += kThreads) {
+                if constexpr (std::is_same<C, float4>::value) s_dvw[i] = (&P.stencil->dvaldf[0][0][0])[i];
+                else s_dvw[i] = make_float2((&P.stencil->dval32[0][0][0])[i], 0.f);
+            }
+            build_res_map<C>(P, pr0, pr1, rrows, rmeta, rcols, rgoff, s_rm);
+            if (P.pk) {
+                pack_explicit<C>(P, rrows, rmeta, rgoff, s_rm);
+                __syncthreads();
+            }
+            rv_local.rows = rrows;
+            rv_local.meta = rmeta;
+            rv_local.cols = rcols;
+            rv_local.goff = rgoff;
+            rv = &rv_local;
+        }
+    }
     const int n_items = (r1 - r0) * R;  // (node, column) pairs owned by this CTA
     const int my_c = tid % R;           // column of every item this thread handles
     const size_t base_o = (size_t)3 * r0 * R;
@@ -616,6 +1102,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     int trace_it = 0;
 
     if (tid == 0) mbar_init(&s_mbar, 1);
+    grid_barrier_init();
     if (tid < R) {
         s_done[tid] = 0;
         s_status[tid] = FE_OK;
@@ -787,25 +1274,43 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         }
 
         // ---- [A] products and fused dots ----
+        // The CTA's last warp (the lightest product rows come last) takes the
+        // reciprocals the next scalars need: 1/gamma = conj(gamma) / |gamma|^2
+        // and 1/alpha = conj(alpha) / |alpha|^2 of the last iteration.
+        if (tid >= kThreads - R) {
+            const int c = kThreads - 1 - tid;
+            if (s_active[c] && !s_first[c]) {
+                const double ig = rcp64(s_gam_r[c] * s_gam_r[c] + s_gam_i[c] * s_gam_i[c]);
+                const double ia = rcp64(s_al_r[c] * s_al_r[c] + s_al_i[c] * s_al_i[c]);
+                s_igam_r[c] = s_gam_r[c] * ig;
+                s_igam_i[c] = -s_gam_i[c] * ig;
+                s_ial_r[c] = s_al_r[c] * ia;
+                s_ial_i[c] = -s_al_i[c] * ia;
+            }
+        }
         FE_TRACE_MARK(0);
         if (s_any_refresh) {
             double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+            float facc[22] = {};
             if (!product_step<TM, R, 11>(P, cta, stage_fits, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, s_refresh,
-                                         s_any_refresh, s_cols, acc, trace_it))
+                                         s_any_refresh, s_cols, acc, facc, trace_it, rv))
                 goto out;
             FE_TRACE_MARK(2);
-            cta_colsum<R, 11>(acc, s_red, s_in);
+            if constexpr (kDFV) cta_colsum_df<R, 11>(facc, s_red, s_in);
+            else cta_colsum<R, 11>(acc, s_red, s_in);
             FE_TRACE_MARK(3);
-            if (!grid_reduce<11 * R>(P, cta, s_in, s_out)) goto out;
+            if (!grid_reduce<11 * R, kDFV>(P, cta, s_in, s_out)) goto out;
         } else {
             double acc[5] = {0, 0, 0, 0, 0};
+            float facc[10] = {};
             if (!product_step<TM, R, 5>(P, cta, stage_fits, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, s_refresh,
-                                        s_any_refresh, s_cols, acc, trace_it))
+                                        s_any_refresh, s_cols, acc, facc, trace_it, rv))
                 goto out;
             FE_TRACE_MARK(2);
-            cta_colsum<R, 5>(acc, s_red, s_in);
+            if constexpr (kDFV) cta_colsum_df<R, 5>(facc, s_red, s_in);
+            else cta_colsum<R, 5>(acc, s_red, s_in);
             FE_TRACE_MARK(3);
-            if (!grid_reduce<5 * R>(P, cta, s_in, s_out)) goto out;
+            if (!grid_reduce<5 * R, kDFV>(P, cta, s_in, s_out)) goto out;
         }
         FE_TRACE_MARK(4);
         // ---- [B] scalars ----
@@ -842,7 +1347,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             }
             continue;
         }
-        // B2: Chronopoulos-Gear scalars (exact p^T A p after a replacement)
+        // B2: Chronopoulos-Gear scalars (exact p^T A p after a replacement).
+        // 1/gamma_old and 1/alpha_old come from the product phase (taken from
+        // the gamma and the rounded alpha of the last iteration, the alpha
+        // that updated x and r), so beta = gamma (1/gamma_old) and e = delta -
+        // beta gamma (1/alpha_old) need no division: the one reciprocal on the
+        // dependent chain is that of |e|^2.  FP64 operations of one thread
+        // have a long latency on this GPU.
         if (tid < R) {
             const int c = tid;
             if (s_active[c]) {
@@ -851,9 +1362,9 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                 double br = 0.0, bi = 0.0, er = dr, ei = di;
                 if (!s_first[c]) {
                     // beta = gamma / gamma_old
-                    const double ig = rcp64(s_gam_r[c] * s_gam_r[c] + s_gam_i[c] * s_gam_i[c]);
-                    br = (gr * s_gam_r[c] + gi * s_gam_i[c]) * ig;
-                    bi = (gi * s_gam_r[c] - gr * s_gam_i[c]) * ig;
+                    br = gr * s_igam_r[c] - gi * s_igam_i[c];
+                    bi = gr * s_igam_i[c] + gi * s_igam_r[c];
+                    if constexpr (kDFV) s_b4[c] = from_c128<float4>(make_double2(br, bi));
                     if (s_refresh[c]) {
                         // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
                         const double e12r = s_out[5 * R + c] + s_out[7 * R + c];
@@ -865,14 +1376,15 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     } else {
                         // delta - beta gamma / alpha_old
                         const double tr = br * gr - bi * gi, ti = br * gi + bi * gr;
-                        const double ia = rcp64(s_al_r[c] * s_al_r[c] + s_al_i[c] * s_al_i[c]);
-                        er = dr - (tr * s_al_r[c] + ti * s_al_i[c]) * ia;
-                        ei = di - (ti * s_al_r[c] - tr * s_al_i[c]) * ia;
+                        er = dr - (tr * s_ial_r[c] - ti * s_ial_i[c]);
+                        ei = di - (tr * s_ial_i[c] + ti * s_ial_r[c]);
                     }
+                } else if constexpr (kDFV) {
+                    s_b4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 const double ed = er * er + ei * ei;
                 const double gg = gr * gr + gi * gi;
-                if (!(ed > 0.0) || !(ed < 1e300) || !(gg > 0.0)) {
+                if (!(ed > 0.0) || !(ed < 1e300) || !(gg > 0.0) || !(gg < 1e300)) {
                     if (s_first[c]) {  // breakdown right after a (re)start
                         s_active[c] = 0;
                         s_done[c] = 1;
@@ -883,8 +1395,14 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     }
                 } else {
                     const double ie = rcp64(ed);
-                    s_al_r[c] = (gr * er + gi * ei) * ie;
-                    s_al_i[c] = (gi * er - gr * ei) * ie;
+                    const double ar = (gr * er + gi * ei) * ie, ai = (gi * er - gr * ei) * ie;
+                    s_al_r[c] = ar;
+                    s_al_i[c] = ai;
+                    if constexpr (kDFV) {
+                        const float4 a4 = from_c128<float4>(make_double2(ar, ai));
+                        s_a4[c] = a4;
+                        s_na4[c] = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
+                    }
                     s_be_r[c] = br;
                     s_be_i[c] = bi;
                     s_gam_r[c] = gr;
@@ -922,8 +1440,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             constexpr int kChunk = (kThreads / (3 * R)) * (3 * R);
             const int n3 = 3 * n_items;
             if constexpr (kDFV) {  // the same update in FP32-pair arithmetic
-                const float4 a4 = from_c128<float4>(alpha), na4 = from_c128<float4>(nalpha);
-                const float4 b4 = from_c128<float4>(beta);
+                const float4 a4 = s_a4[my_c], na4 = s_na4[my_c], b4 = s_b4[my_c];
                 float4* ex = (float4*)s_exch;
                 for (int base = 0; base < n3; base += kChunk) {
                     const int i = base + tid;
@@ -1042,10 +1559,40 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 struct Workspace {
-    DevBuf b, x, r, u, p, s, uM, pM, w, partial, result, sync, rep, trace;
+    DevBuf b, x, r, u, p, s, uM, pM, w, partial, result, sync, rep, trace, pk;
 };
 
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic; static shared memory adds ~20 KB
+
+// Sizes the resident product map of an R = 1 class-path launch (P.res and
+// its shared memory); `rows_per_cta` bounds a CTA's product rows.  The halo
+// buffer then takes the rest of the budget: three segments of at most
+// rows + 2 * res_tmid nodes each fit it whenever the estimate below does.
+template <typename C>
+bool size_res_map(SolveParams& P, int64_t rows_per_cta, size_t& dyn) {
+    P.res = 0;
+    P.res_bytes = 0;
+    if (!P.row_class || P.halo <= 0) return false;
+    const int64_t m = (rows_per_cta + kRowsPerWarpR1 + 1) & ~1ll;  // rows plus the padding of the explicit slots
+    const int64_t res_bytes =
+        (m * (int64_t)(sizeof(int) + sizeof(int2) + 27 * sizeof(int)) + (m / kExplRows + 2) * (int64_t)sizeof(int) +
+         15) & ~15ll;
+    const int64_t fixed = (int64_t)P.red_bytes + res_bytes;
+    // the halo also holds the true-residual phase's column staging; shared
+    // memory is kept to what is needed, since the rest of the SM's 256 KB is
+    // its L1 cache, which catches the register spills of 1024 threads
+    const int64_t need = std::max<int64_t>(3 * (m + 2 * (int64_t)P.res_tmid + 24) * 3 * (int64_t)sizeof(C) + 3 * 32,
+                                           (int64_t)kWarps * kColsPerWarp * (int64_t)sizeof(int));
+    if (fixed + need > (int64_t)kSmemBudget || m > (1 << 20)) return false;
+    P.res = 1;
+    P.res_rows_max = (int)m;
+    P.res_bytes = (int)res_bytes;
+    P.col_bytes = 0;
+    P.stage = 1;
+    P.halo_bytes = (need + 15) & ~15ll;
+    dyn = (size_t)(fixed + P.halo_bytes);
+    return true;
+}
 
 template <typename T, int R>
 fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
@@ -1054,6 +1601,7 @@ fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
     // one CTA per SM; the reduction scratch and (when it fits) the CTA's
     // vector halo live in dynamic shared memory
     P.n_cta = std::min(ctx->num_sms, std::max(1, P.n_rows));
+    P.part_half = (int64_t)P.n_cta * kMaxNV * R;
     P.red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
     P.col_bytes = R == 1 ? (int)(kWarps * kColsPerWarp * sizeof(int)) : 0;
     // product phases: a CTA's range costs at most total / n_cta plus one row
@@ -1062,7 +1610,10 @@ fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
     const int64_t halo_bytes = (rows_per_cta + 2 * (int64_t)P.halo + 2) * 3 * R * (int64_t)sizeof(C) + 64;
     P.stage = (P.halo > 0 && (size_t)P.red_bytes + P.col_bytes + (size_t)halo_bytes <= kSmemBudget) ? 1 : 0;
     P.halo_bytes = P.stage ? halo_bytes : 0;
-    const size_t dyn = (size_t)P.red_bytes + P.col_bytes + (P.stage ? (size_t)halo_bytes : 0);
+    size_t dyn = (size_t)P.red_bytes + P.col_bytes + (P.stage ? (size_t)halo_bytes : 0);
+    P.res = 0;
+    P.res_bytes = 0;
+    if constexpr (kClassPath<T> && R == 1) size_res_map<C>(P, rows_per_cta, dyn);
     FE_CUDA(cudaFuncSetAttribute((const void*)k_solve<T, R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     int per_sm = 0;
     FE_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_solve<T, R>, kThreads, dyn));
@@ -1122,6 +1673,7 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
         SolveParams& P = Ps[i];
         P = jobs[i]->P;
         P.n_cta = n_cta[i];
+        P.part_half = (int64_t)P.n_cta * kMaxNV * R;
         P.red_bytes = red_bytes;
         P.col_bytes = col_bytes;
         const int64_t rows_per_cta =
@@ -1130,10 +1682,16 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
         const size_t need = (size_t)red_bytes + col_bytes + (size_t)halo_bytes;
         P.stage = (P.halo > 0 && need <= kSmemBudget) ? 1 : 0;
         if (P.stage) dyn = std::max(dyn, need);
+        P.res = 0;
+        P.res_bytes = 0;
+        if constexpr (kClassPath<T> && R == 1) {
+            size_t dres = 0;
+            if (size_res_map<C>(P, rows_per_cta, dres)) dyn = std::max(dyn, dres);
+        }
         cta0[i + 1] = cta0[i] + n_cta[i];
         FE_CUDA(cudaMemsetAsync(P.sync, 0, sizeof(SyncState), ctx->stream));
     }
-    for (int i = 0; i < n; ++i) Ps[i].halo_bytes = (int64_t)dyn - red_bytes - col_bytes;
+    for (int i = 0; i < n; ++i) Ps[i].halo_bytes = (int64_t)dyn - red_bytes - Ps[i].col_bytes - Ps[i].res_bytes;
     const int grid = cta0[n];
     DevBuf dparams, dcta;
     FE_TRY(dev_alloc(ctx->stream, dparams, (size_t)n * sizeof(SolveParams)));

@@ -84,3 +84,26 @@ def test_recorded_traffic_follows_the_kernel_sources(bench, monkeypatch):
     assert bench.recorded_traffic("config3", "df") is None
     monkeypatch.setattr(bench, "kernel_hash", lambda: "0" * 16)
     assert bench.recorded_traffic("config2", "df") is None
+
+
+def test_method_bytes_per_product_match_the_worked_figures(bench):
+    # The survey's worked figures for the 3-wavelength cube (748 658 blocks,
+    # 29 666 nodes, 88 998 unknowns), one column: 58.4 MB per complex64
+    # product and 113.8 MB per complex128 (or FP32-pair) product.
+    c2 = {"nnzb": 748658, "n_nodes": 29666, "n_dof": 88998}
+    assert bench.product_bytes(c2, 8, 1) == 748658 * 76 + 29667 * 4 + 2 * 88998 * 8
+    assert round(bench.product_bytes(c2, 8, 1) / 1e6, 1) == 58.4
+    assert round(bench.product_bytes(c2, 16, 1) / 1e6, 1) == 113.8
+    # R columns: the vectors scale, the matrix does not
+    assert bench.product_bytes(c2, 8, 32) - bench.product_bytes(c2, 8, 1) == 2 * 88998 * 8 * 31
+
+
+def test_method_products_count_the_slowest_column_of_each_launch(bench):
+    rep = [{"iterations": 10, "outer": 3}, {"iterations": 12, "outer": 2},
+           {"iterations": 7, "outer": 2}, {"iterations": 9, "outer": 4}]
+    # two launches of two columns: 12 + (3 - 2) and 9 + (4 - 2) inner products;
+    # 3 + 4 true-residual products
+    assert bench.method_products(rep, 2) == (12 + 1 + 9 + 2, 3 + 4)
+    # one column per launch: a column with two passes has no intermediate refresh
+    assert bench.method_products(rep[:1], 1) == (10 + 1, 3)
+    assert bench.method_products(rep[1:2], 1) == (12, 2)
