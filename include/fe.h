@@ -191,13 +191,20 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
  * vals_c128[nnzb*9*2 doubles], vals_c64[nnzb*9*2 floats] (FE_PREC_MIXED only,
  * else FE_ERR_INVALID_ARG), dinv_c128[n_nodes*9*2 doubles]. */
 fe_status fe_system_export(fe_ctx* ctx, const fe_system* s, void* vals_c128, void* vals_c64, void* dinv_c128);
-/* Regular rows (interior nodes whose eight elements are active, of one
+/* Block dictionary (complex64 and FP32-pair systems): equal local
+ * configurations of the voxel mesh give bitwise equal 3x3 blocks, so the
+ * system also keeps each distinct block once (at most 4096 of them) with an
+ * index per stored block; single-column solves read explicit rows through it
+ * when it fits in shared memory.  dict_blocks counts the distinct blocks, 0
+ * when there are too many (the products then read the stored values).
+ *
+ * Regular rows (interior nodes whose eight elements are active, of one
  * material, with no outer or PEC face) all carry the same 27 blocks per
  * material; the Krylov products read them from a per-material stencil instead
  * of the stored blocks.  The counts say how many rows take each path. */
 typedef struct fe_system_stats {
     int32_t precision;         /* as assembled */
-    int32_t reserved;
+    int32_t dict_blocks;       /* distinct 3x3 blocks in the block dictionary (0: none) */
     int64_t n_rows, nnzb;      /* block rows, stored blocks */
     int64_t rows_general;      /* regular rows with a general 3x3-block stencil */
     int64_t rows_diagonal;     /* regular rows whose stencil blocks are real multiples of I3 */

@@ -414,10 +414,12 @@ static void system_free(fe_system* s) {
     half_release(s);
     cudaStream_t st = s->ctx->stream;
     for (DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
-                      &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix, &s->bicp_l,
+                      &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix, &s->dict_idx,
+                      &s->dict_vals, &s->bicp_l,
                       &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         dev_free(st, *b);
     s->bicp_n_sub = 0;
+    s->n_dict = 0;
 }
 
 }  // namespace fe
@@ -575,6 +577,7 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
         s->rows_diagonal = (int64_t)hc[1];
         s->blocks_explicit = (int64_t)hc[2];
     }
+    if ((e = build_block_dict(ctx, s)) != FE_OK) return fail(e);
     *out = s;
     return FE_OK;
 }
@@ -586,7 +589,7 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
     }
     const fe_mesh* m = s->mesh;
     out->precision = s->precision;
-    out->reserved = 0;
+    out->dict_blocks = s->n_dict;
     out->n_rows = m->n_act;
     out->nnzb = m->nnzb;
     out->rows_general = s->rows_general;
@@ -594,7 +597,8 @@ fe_status fe_system_info(const fe_system* s, fe_system_stats* out) {
     out->blocks_explicit = s->blocks_explicit;
     int64_t bytes = 0;
     for (const DevBuf* b : {&s->tables, &s->val64, &s->val32, &s->valdf, &s->dinv64, &s->dinv32, &s->dinvdf,
-                            &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix, &s->bicp_l,
+                            &s->row_class, &s->stencil, &s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix,
+                            &s->dict_idx, &s->dict_vals, &s->bicp_l,
                             &s->bicp_linv, &s->bicp_tpos, &s->bicp_tab, &s->bicp_lev, &s->bicp_nlev})
         bytes += (int64_t)b->bytes;
     out->device_bytes = bytes + half_bytes(s);

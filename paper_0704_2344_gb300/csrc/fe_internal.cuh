@@ -178,6 +178,12 @@ struct fe_system {
     int64_t cost_total_alu = 0;
     // prefix sum of the stored blocks of explicit rows (rows of no class)
     fe::DevBuf expl_prefix;          // int [n_act + 1]; expl_prefix[n_act] = blocks_explicit
+    // Block dictionary (complex64 and FP32-pair systems): the distinct 3x3
+    // blocks once, in the inner precision, entry (alpha, beta) of block d at
+    // [9 d + 3 alpha + beta], and each stored block's index.  n_dict = 0: none.
+    fe::DevBuf dict_idx;             // uint16 [nnzb]
+    fe::DevBuf dict_vals;            // float2 or float4 [n_dict * 9]
+    int n_dict = 0;
     int cost_min[2] = {1, 1}, cost_max[2] = {1, 1};  // bounds of one row's cost (complex64, FP32 pairs)
     int64_t rows_general = 0, rows_diagonal = 0, blocks_explicit = 0;  // rows per product path
     // Block incomplete Cholesky factor (Section 3.1.5.3): node rows split into
@@ -197,6 +203,8 @@ struct fe_system {
 
 namespace fe {
 constexpr int kMaxClasses = 4;
+constexpr int kMaxDict = 4096;  // distinct blocks a dictionary may hold
+fe_status build_block_dict(fe_ctx* ctx, fe_system* s);
 // Per-class stencils of regular rows, indexed [class][alpha][block k][beta];
 // kind: 0 = no regular row, 1 = general complex blocks, 2 = real diagonal
 // blocks (the homogeneous interior with eps_r = 1 and s = 1); dval holds the

@@ -106,8 +106,16 @@ static fe_status with_inner_type(int prec, F&& f) {
 
 // Entries of the packed explicit rows a single-column complex64 or
 // FP32-pair launch copies its explicit rows into (0: none).
+// A system's block dictionary serves single-column solves when it holds at
+// most kDictSmemMax bytes (it is copied into every CTA's shared memory).
+constexpr size_t kDictSmemMax = 64 * 1024;
+static bool dict_usable(const fe_system* s, int prec, int R) {
+    return R == 1 && prec != FE_PREC_FP64 && s->n_dict > 0 &&
+           (size_t)s->n_dict * 9 * inner_bytes(prec) <= kDictSmemMax;
+}
+
 static int64_t packed_entries(const fe_system* s, int prec, int R) {
-    if (R != 1 || prec == FE_PREC_FP64 || !s->expl_prefix.ptr) return 0;
+    if (R != 1 || prec == FE_PREC_FP64 || !s->expl_prefix.ptr || dict_usable(s, prec, R)) return 0;
     return 9 * s->blocks_explicit;
 }
 
@@ -122,7 +130,7 @@ static fe_status alloc_workspace(cudaStream_t st, int64_t n_dof, int R, int prec
                     std::make_pair(&w.pM, split_copies(prec, R) ? nv * esz : (size_t)16), std::make_pair(&w.w, nv * esz),
                     std::make_pair(&w.partial, (size_t)max_cta * kMaxNV * R * sizeof(double)),
                     std::make_pair(&w.result, (size_t)kMaxNV * R * sizeof(double)),
-                    std::make_pair(&w.sync, sizeof(SyncState)),
+                    std::make_pair(&w.sync, sync_bytes(max_cta)),
                     std::make_pair(&w.rep, (size_t)R * (3 * sizeof(int) + sizeof(double)) + 64)}) {
         const fe_status e = dev_alloc(st, *pr.first, pr.second);
         if (e != FE_OK) {
@@ -189,6 +197,11 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.trace = (unsigned long long*)w.trace.ptr;
     P.pk = classes ? w.pk.ptr : nullptr;
     P.expl_prefix = classes ? (const int*)s->expl_prefix.ptr : nullptr;
+    if (classes && dict_usable(s, prec, R)) {
+        P.dict_idx = (const uint16_t*)s->dict_idx.ptr;
+        P.dictM = s->dict_vals.ptr;
+        P.n_dict = s->n_dict;
+    }
     // lexicographic node ranks: a neighbour is at most one plane, one line
     // and one node away
     P.halo = (m->nx + 1) * (m->ny + 1) + (m->nx + 1) + 1;
@@ -257,7 +270,7 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
             k_gather_cols<<<gb, 256, 0, st>>>(d_x, nrhs, c0, nc, (double2*)w.x.ptr, R, n_dof);
             count_launches(1);
         }
-        cudaMemsetAsync(w.sync.ptr, 0, sizeof(SyncState), st);
+        cudaMemsetAsync(w.sync.ptr, 0, sync_bytes(ctx->num_sms), st);
         SolveParams P;
         fill_params(P, s, w, R, prec, o, use_x0);
         int* ri = P.rep_status;
@@ -658,7 +671,7 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     }
     take(w.partial, (size_t)max_cta * kMaxNV * R * sizeof(double));
     take(w.result, (size_t)kMaxNV * R * sizeof(double));
-    take(w.sync, sizeof(SyncState));
+    take(w.sync, sync_bytes(max_cta));
     take(w.rep, (size_t)R * (3 * sizeof(int) + sizeof(double)) + 64);
     if (off > kStaticScratchBytes) {
         set_error("fe_solve_rhs_noalloc: needs %zu bytes of scratch, the static array holds %zu (n_dof x nrhs too "
@@ -667,7 +680,7 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
         return FE_ERR_INVALID_ARG;
     }
     cudaStream_t st = ctx->stream;
-    FE_CUDA(cudaMemsetAsync(w.sync.ptr, 0, sizeof(SyncState), st));  // the array keeps the previous call's contents
+    FE_CUDA(cudaMemsetAsync(w.sync.ptr, 0, sync_bytes(ctx->num_sms), st));  // the array keeps the previous call's contents
     SolveParams P;
     fill_params(P, s, w, R, prec, opt, use_x0 != 0);
     P.trace = nullptr;

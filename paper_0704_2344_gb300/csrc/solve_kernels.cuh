@@ -29,6 +29,11 @@ struct SyncState {
     int err;
     int pad;
 };
+// Barrier state of one launch (zeroed before every launch).
+inline size_t sync_bytes(int n_cta) {
+    (void)n_cta;
+    return sizeof(SyncState);
+}
 
 // Krylov storage.  The solution x, the recurrences (r, u, p, s) and all inner
 // products are FP64; the sparse product of the Krylov loop runs in the
@@ -92,6 +97,13 @@ struct SolveParams {
     // planes.
     void* pk;                 // inner-precision entries [9 * explicit blocks]
     const int* expl_prefix;   // [n_rows + 1] stored blocks of explicit rows before each row
+    // Block dictionary (with the map, when it fits): each CTA copies the
+    // distinct blocks and its explicit rows' block indices into shared
+    // memory, and explicit rows then read nothing from global memory but the
+    // product input's halo.  NULL: packed rows or planes.
+    const uint16_t* dict_idx;  // [nnzb] dictionary index of each stored block
+    const void* dictM;         // [n_dict * 9] distinct blocks in the inner precision
+    int n_dict;
     int* rep_status;
     int* rep_iters;
     int* rep_outer;
@@ -137,6 +149,7 @@ __device__ __forceinline__ unsigned load_acquire(const unsigned* count) {
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(count) : "memory");
     return v;
 }
+
 
 __device__ __forceinline__ void grid_barrier_init() {
     if (threadIdx.x == 0) g_bar_epoch = 0u;
@@ -372,7 +385,7 @@ struct ResMap {
 
 template <typename C>
 __device__ __noinline__ void build_res_map(const SolveParams& P, int pr0, int pr1, int* rows, int2* meta, int* cols,
-                                           int* goff, ResMap& rm) {
+                                           int* goff, uint16_t* bidx, C* dict, ResMap& rm) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int n = pr1 - pr0;
     int* keys = cols;  // scratch until the column map is written
@@ -382,7 +395,9 @@ __device__ __noinline__ void build_res_map(const SolveParams& P, int pr0, int pr
         const int cls = P.row_class ? P.row_class[row] : -1;
         const int kind = cls >= 0 ? P.stencil->kind[cls] : 0;
         const int nb = P.rp[row + 1] - P.rp[row];
-        keys[i] = kind == 2 ? 21 : (kind == 1 ? 20 : max(0, min(19, 27 - nb)));
+        // with the dictionary, general-stencil rows are read like explicit
+        // ones (their blocks are in it too)
+        keys[i] = kind == 2 ? 21 : ((kind == 1 && !bidx) ? 20 : max(0, min(19, 27 - nb)));
     }
     if (tid < 3) {
         s_lo[tid] = 0x7fffffff;
@@ -500,8 +515,11 @@ __device__ __noinline__ void build_res_map(const SolveParams& P, int pr0, int pr
                 e = (int)(((long long)rm.soff[a] + 3ll * c * (long long)sizeof(C) - rm.a0[a]) / (long long)sizeof(C));
             }
             cols[i * 27 + lane] = e;
+            if (bidx) bidx[i * 27 + lane] = __ldg(P.dict_idx + mt.x + lane);
         }
     }
+    if (dict)
+        for (int i = tid; i < 9 * P.n_dict; i += kThreads) dict[i] = __ldg((const C*)P.dictM + i);
     __syncthreads();
 }
 
@@ -564,7 +582,10 @@ struct ResView {
     const int* cols;
     const int* goff;  // packed entries before each explicit warp group
     const float2* dvw;  // diagonal-stencil weights [class][alpha][27] in shared memory (FP32 pair, or .x alone)
+    const uint16_t* bidx;  // per slot, 27 dictionary indices of its blocks (shared memory; NULL: no dictionary)
+    const void* dict;      // the dictionary in shared memory
     const ResMap* rm;
+    unsigned long long* wtrace;  // diagnostics: per-warp stamps of one traced iteration (or NULL)
 };
 
 // Component alpha of a diagonal-stencil row (27 real weights, shared
@@ -668,9 +689,61 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
         const int n_eg = nexpl / kExplRows;  // explicit groups (kExplRows rows), then class groups (ten rows)
         const int n_groups = n_eg + (n - nexpl + kRowsPerWarpR1 - 1) / kRowsPerWarpR1;
         const bool packed = P.pk != nullptr;
+        int n_eg_done = 0, n_cg_done = 0;
         for (int k = 0; k * kWarps < n_groups; ++k) {
             const int g = k * kWarps + ((k & 1) ? kWarps - 1 - warp : warp);
             if (g >= n_groups) continue;
+            if (g < n_eg) ++n_eg_done;
+            else ++n_cg_done;
+            if (g < n_eg && rv->bidx) {
+                // explicit rows through the block dictionary: lane 3j + alpha
+                // walks the blocks of row j, component alpha, reading the
+                // block's index, its three entries and the three vector
+                // entries from shared memory
+                const int j = lane / 3;
+                const int slot = g * kExplRows + j;
+                const bool valid = lane < 3 * kExplRows && rv->rows[slot] >= 0;
+                const int2 mt = valid ? rv->meta[slot] : make_int2(0, 0);
+                const int nb = mt.y & 0xff;
+                const int* rc = rv->cols + slot * 27;
+                const uint16_t* rb = rv->bidx + slot * 27;
+                const C* dct = (const C*)rv->dict + 3 * al;
+                const C* xv = kStaged ? xs : uM;
+                C y;
+                if constexpr (std::is_same<C, float4>::value) {
+                    float a4[4] = {0.f, 0.f, 0.f, 0.f};
+                    for (int kk = 0; kk < nb; ++kk) {
+                        const int e = rc[kk];
+                        const C* m = dct + 9 * (int)rb[kk];
+                        dfc_mac(a4, m[0], kStaged ? xv[e] : ld_cg(xv + e));
+                        dfc_mac(a4, m[1], kStaged ? xv[e + 1] : ld_cg(xv + e + 1));
+                        dfc_mac(a4, m[2], kStaged ? xv[e + 2] : ld_cg(xv + e + 2));
+                    }
+                    y = df_result(a4);
+                } else {
+                    using Tr = decltype(C{}.x);
+                    Tr ar = 0, ai = 0;
+                    for (int kk = 0; kk < nb; ++kk) {
+                        const int e = rc[kk];
+                        const C* m = dct + 9 * (int)rb[kk];
+                        const C m0 = m[0], m1 = m[1], m2 = m[2];
+                        const C x0 = kStaged ? xv[e] : ld_cg(xv + e), x1 = kStaged ? xv[e + 1] : ld_cg(xv + e + 1),
+                                x2 = kStaged ? xv[e + 2] : ld_cg(xv + e + 2);
+                        ar += m0.x * x0.x - m0.y * x0.y + m1.x * x1.x - m1.y * x1.y + m2.x * x2.x - m2.y * x2.y;
+                        ai += m0.x * x0.y + m0.y * x0.x + m1.x * x1.y + m1.y * x1.x + m2.x * x2.y + m2.y * x2.x;
+                    }
+                    y = mk(ar, ai);
+                }
+                if (valid) {
+                    const int row = rv->rows[slot];
+                    const size_t o = (size_t)3 * row + al;
+                    w[o] = y;
+                    C sy = y;
+                    if (refresh) sy = row_component<C, false>(valM, P.stride, P.col + mt.x, mt.x, mt.x + nb, al, pM, 0);
+                    dots(o, y, refresh, sy);
+                }
+                continue;
+            }
             if (g < n_eg && packed) {
                 // explicit rows from the packed copy: lane 3j + alpha walks the
                 // blocks of row j, component alpha; each step loads 3 J_k
@@ -755,6 +828,10 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
                 dots(o, y, refresh, sy);
             }
         }
+        if (rv->wtrace && lane == 0) {
+            rv->wtrace[warp] = globaltimer_ns();
+            rv->wtrace[kWarps + warp] = (unsigned long long)(1000 * n_eg_done + n_cg_done);
+        }
     } else if (R == 1) {
         // one thread per (row, component): ten rows per warp, their column
         // indices staged in shared memory first
@@ -821,7 +898,7 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
 // Diagnostics (FE_TRACE=1): every CTA stamps the end of each phase of its
 // first kTraceIters iterations, [cta][iteration][phase]; after those stamps
 // come kTraceStats values per CTA describing its product rows.
-constexpr int kTraceStats = 8;
+constexpr int kTraceStats = 8 + 2 * kWarps;  // row counts, then per warp the end of its product rows and its groups
 #define FE_TRACE_MARK(k)                                                                        \
     do {                                                                                        \
         if (P.trace && tid == 0 && trace_it < kTraceIters)                                      \
@@ -1071,7 +1148,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     constexpr bool kRes = kClassPath<TM> && R == 1;
     __shared__ ResMap s_rm;
     __shared__ float2 s_dvw[kRes ? kMaxClasses * 81 : 1];
-    ResView rv_local{nullptr, nullptr, nullptr, nullptr, s_dvw, &s_rm};
+    ResView rv_local{nullptr, nullptr, nullptr, nullptr, s_dvw, nullptr, nullptr, &s_rm, nullptr};
     const ResView* rv = nullptr;
     if constexpr (kRes) {
         if (P.res && pr1 - pr0 + kRowsPerWarpR1 <= P.res_rows_max) {
@@ -1079,12 +1156,16 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             int2* rmeta = (int2*)(rrows + P.res_rows_max);
             int* rcols = (int*)(rmeta + P.res_rows_max);
             int* rgoff = rcols + 27 * P.res_rows_max;
+            uint16_t* rbidx = P.dictM ? (uint16_t*)(rgoff + (P.res_rows_max / kExplRows + 2)) : nullptr;
+            C* rdict = P.dictM ? (C*)(((uintptr_t)(rbidx + 27 * P.res_rows_max) + 15) & ~(uintptr_t)15) : nullptr;
             for (int i = tid; i < kMaxClasses * 81; i += kThreads) {
                 if constexpr (std::is_same<C, float4>::value) s_dvw[i] = (&P.stencil->dvaldf[0][0][0])[i];
                 else s_dvw[i] = make_float2((&P.stencil->dval32[0][0][0])[i], 0.f);
             }
-            build_res_map<C>(P, pr0, pr1, rrows, rmeta, rcols, rgoff, s_rm);
-            if (P.pk) {
+            build_res_map<C>(P, pr0, pr1, rrows, rmeta, rcols, rgoff, rbidx, rdict, s_rm);
+            rv_local.bidx = rbidx;
+            rv_local.dict = rdict;
+            if (P.pk && !P.dictM) {
                 pack_explicit<C>(P, rrows, rmeta, rgoff, s_rm);
                 __syncthreads();
             }
@@ -1289,6 +1370,9 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             }
         }
         FE_TRACE_MARK(0);
+        if (rv) rv_local.wtrace = (P.trace && trace_it == 20)
+                                      ? P.trace + (size_t)P.n_cta * kTraceIters * kTracePhases + (size_t)cta * kTraceStats + 8
+                                      : nullptr;
         if (s_any_refresh) {
             double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             float facc[22] = {};
@@ -1569,14 +1653,17 @@ constexpr size_t kSmemBudget = 200 * 1024;  // dynamic; static shared memory add
 // buffer then takes the rest of the budget: three segments of at most
 // rows + 2 * res_tmid nodes each fit it whenever the estimate below does.
 template <typename C>
-bool size_res_map(SolveParams& P, int64_t rows_per_cta, size_t& dyn) {
+bool size_res_map_once(SolveParams& P, int64_t rows_per_cta, size_t& dyn) {
     P.res = 0;
     P.res_bytes = 0;
     if (!P.row_class || P.halo <= 0) return false;
     const int64_t m = (rows_per_cta + kRowsPerWarpR1 + 1) & ~1ll;  // rows plus the padding of the explicit slots
-    const int64_t res_bytes =
-        (m * (int64_t)(sizeof(int) + sizeof(int2) + 27 * sizeof(int)) + (m / kExplRows + 2) * (int64_t)sizeof(int) +
-         15) & ~15ll;
+    int64_t res_bytes = m * (int64_t)(sizeof(int) + sizeof(int2) + 27 * sizeof(int)) +
+                        (m / kExplRows + 2) * (int64_t)sizeof(int);
+    if (P.dictM)  // per-slot block indices, then the dictionary (16-byte aligned)
+        res_bytes = ((res_bytes + 27 * m * (int64_t)sizeof(uint16_t) + 15) & ~15ll) +
+                    9 * (int64_t)P.n_dict * (int64_t)sizeof(C);
+    res_bytes = (res_bytes + 15) & ~15ll;
     const int64_t fixed = (int64_t)P.red_bytes + res_bytes;
     // the halo also holds the true-residual phase's column staging; shared
     // memory is kept to what is needed, since the rest of the SM's 256 KB is
@@ -1592,6 +1679,16 @@ bool size_res_map(SolveParams& P, int64_t rows_per_cta, size_t& dyn) {
     P.halo_bytes = (need + 15) & ~15ll;
     dyn = (size_t)(fixed + P.halo_bytes);
     return true;
+}
+
+template <typename C>
+bool size_res_map(SolveParams& P, int64_t rows_per_cta, size_t& dyn) {
+    if (size_res_map_once<C>(P, rows_per_cta, dyn)) return true;
+    if (!P.dictM) return false;
+    P.dictM = nullptr;  // without the dictionary, explicit rows read the planes
+    P.dict_idx = nullptr;
+    P.n_dict = 0;
+    return size_res_map_once<C>(P, rows_per_cta, dyn);
 }
 
 template <typename T, int R>
@@ -1689,7 +1786,7 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
             if (size_res_map<C>(P, rows_per_cta, dres)) dyn = std::max(dyn, dres);
         }
         cta0[i + 1] = cta0[i] + n_cta[i];
-        FE_CUDA(cudaMemsetAsync(P.sync, 0, sizeof(SyncState), ctx->stream));
+        FE_CUDA(cudaMemsetAsync(P.sync, 0, sync_bytes(P.n_cta), ctx->stream));
     }
     for (int i = 0; i < n; ++i) Ps[i].halo_bytes = (int64_t)dyn - red_bytes - Ps[i].col_bytes - Ps[i].res_bytes;
     const int grid = cta0[n];

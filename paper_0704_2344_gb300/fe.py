@@ -60,7 +60,7 @@ class fe_mesh_stats(C.Structure):
 
 
 class fe_system_stats(C.Structure):
-    _fields_ = [("precision", C.c_int32), ("reserved", C.c_int32)] + [
+    _fields_ = [("precision", C.c_int32), ("dict_blocks", C.c_int32)] + [
         (n, C.c_int64) for n in ("n_rows", "nnzb", "rows_general", "rows_diagonal", "blocks_explicit",
                                  "device_bytes")]
 
@@ -320,7 +320,7 @@ def fe_system_export(ctx, system, mesh, c128=True, c64=False, dinv=False) -> dic
 def fe_system_info(system) -> dict:
     st = fe_system_stats()
     _check(load().fe_system_info(system, C.byref(st)), "fe_system_info")
-    return {n: int(getattr(st, n)) for n, _ in fe_system_stats._fields_ if n != "reserved"}
+    return {n: int(getattr(st, n)) for n, _ in fe_system_stats._fields_}
 
 
 def fe_system_export_df(ctx, system, mesh) -> np.ndarray:

@@ -376,3 +376,29 @@ def test_solve_config2_full_size(fe, ctx, config2, precision):
     assert res.max() <= 1e-8, (res, rep)
     err = np.linalg.norm(x - xref) / np.linalg.norm(xref)
     assert err <= 1e-6, err
+
+
+@pytest.mark.parametrize("precision", ["df", "mixed"])
+@pytest.mark.parametrize("name", ["config1", "rand2", "config2"])
+def test_block_dictionary_counts_the_distinct_blocks(fe, ctx, name, precision):
+    """The block dictionary lists each distinct block once: its size equals a
+    bitwise count of the distinct blocks in the exported complex128 values
+    (the dictionary's values are the exported ones, rounded to the inner
+    precision, so equal complex128 blocks are equal there too)."""
+    prob = W.config2()[0] if name == "config2" else SMALL[name]()
+    prec = {"df": fe.FE_PREC_DF, "mixed": fe.FE_PREC_MIXED}[precision]
+    m = fe.fe_mesh_create_from(ctx, prob)
+    try:
+        s = fe.fe_assemble(ctx, m, prob.freq_hz, prec)
+        try:
+            info = fe.fe_system_info(s)
+            g = fe.fe_system_export(ctx, s, m, c128=True)["c128"]
+        finally:
+            fe.fe_system_destroy(s)
+    finally:
+        fe.fe_mesh_destroy(m)
+    flat = np.ascontiguousarray(g.reshape(len(g), -1)).view(np.uint64)
+    distinct = np.unique(flat, axis=0).shape[0]
+    assert info["dict_blocks"] == (distinct if distinct <= 4096 else 0)
+    if name == "config2":
+        assert 0 < info["dict_blocks"] <= 4096
