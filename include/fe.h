@@ -356,28 +356,36 @@ fe_status fe_solve_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void
                        const fe_solve_opts* o, void* x_out, int32_t x_on_device, int32_t use_x0,
                        fe_solve_report* rep);
 
-/* Solve without any allocation, for callers that cannot allocate device
- * memory while they run (for example code already inside stream capture, a
- * host thread that must not block on the allocator, or an embedding that owns
- * every allocation of its process).  The paper has no counterpart.
+/* Solve without any allocation.  Some callers cannot let a library allocate
+ * device memory while they run: an application that reserves all device
+ * memory for itself up front (an allocation would fail, or evict its own
+ * data), a host thread with a latency bound that must not wait on the
+ * device allocator (cudaMalloc and cudaFree can synchronise the device), or
+ * an embedding that accounts for every byte of device memory its process
+ * uses.  The paper has no counterpart.
  *
  * Same method and options as fe_solve_rhs, for a caller right-hand side in
- * DEVICE memory: b_dev and x_dev are complex128 [n_dof][nrhs] device buffers
- * (x_dev holds the initial guess when use_x0 = 1), nrhs one of 1, 2, 4, 8,
- * 16, 32.  rep: optional host array of nrhs reports.
+ * DEVICE memory: b_dev and x_dev are complex128 [n_dof][nrhs] buffers in the
+ * device memory of ctx's device (anything else, a host pointer included, is
+ * rejected with FE_ERR_INVALID_ARG before any GPU work); x_dev holds the
+ * initial guess when use_x0 = 1; nrhs is one of 1, 2, 4, 8, 16, 32.  rep:
+ * optional host array of nrhs reports.
  *
  * Scratch: the call keeps all of its workspace in one file-scope device array
  * of 32 MiB (every GPU that loads the library holds it until the process
  * exits); it calls no cudaMalloc / cudaFree and no allocating routine.  The
- * need is about 88 bytes per unknown and right-hand side (mixed precision;
- * 80 in FP64) plus a few KiB, so n_dof * nrhs may reach roughly 380 000; a
- * larger problem is rejected with FE_ERR_INVALID_ARG and a message naming the
- * bytes it would need.  The first call on a device looks the array's device
- * address up (once per device, with that device current); make that first
- * call before any stream capture.  Every call uses the same array: two calls
- * whose GPU work overlaps (two contexts or streams at once) race on it and
- * corrupt each other's results.  The call returns after the solve has
- * finished (it synchronises the context stream to read the reports).
+ * need is 80 bytes per unknown and right-hand side in the FP64 and FP32-pair
+ * modes and 88 in the mixed mode, plus a few KiB, so n_dof * nrhs may reach
+ * about 415 000 (FP64, FP32 pairs) or 380 000 (mixed); a larger problem is
+ * rejected with FE_ERR_INVALID_ARG and a message naming the bytes it would
+ * need.  The first call on a device looks the array's device address up
+ * (once per device, with that device current), so make that first call
+ * before any stream capture; if the device's context is destroyed later (a
+ * device reset), the next call looks it up again.  The call synchronises the
+ * context's stream to read the reports back, so it must not be made while
+ * that stream (or any stream, in global capture mode) is being captured.
+ * Every call uses the same array: two calls whose GPU work overlaps (two
+ * contexts or streams at once) race on it and corrupt each other's results.
  * Errors: as fe_solve_rhs. */
 fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b_dev, void* x_dev,
                                int32_t use_x0, const fe_solve_opts* o, fe_solve_report* rep);
@@ -385,17 +393,22 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
 /* ------------------------------------------------------------------------
  * Serving: a queue of independent scattering problems (each its own voxel
  * box, frequency and plane waves) solved with continuous batching.  The
- * server owns a worker thread and a CUDA stream of its own on the device of
+ * server owns a worker thread and CUDA streams of its own on the device of
  * the context passed to fe_serve_create (whose options, variant, abc_sigma
  * and penalty_s, apply to every request; that context stays free for the
  * caller).  The worker admits queued requests in arrival order while the
- * sum of their estimated device memory stays within the budget, builds each
- * admitted request's mesh, system (Eqs. 1-4) and right-hand sides, and packs
- * the ready requests of one right-hand-side tile width (1, 2, 4, 8, 16 or
- * 32 after padding with zero columns) into one persistent cooperative
- * solve launch: every request gets its own range of CTAs, synchronises only
- * among them and is solved exactly as fe_solve_batch would solve it.
- * Requests that arrive during a launch join the next one.
+ * sum of their estimated device memory stays within the budget, and builds
+ * each admitted request's mesh, system (Eqs. 1-4) and right-hand sides.
+ * Solves then run in segments of seg_iters iterations: each segment is one
+ * persistent cooperative launch per right-hand-side tile width (1, 2, 4, 8,
+ * 16 or 32 after padding with zero columns), the widths side by side on
+ * their own streams; every request has its own range of CTAs, synchronises
+ * only among them, and keeps its Krylov state on the device from segment to
+ * segment.  Between segments finished requests are handed out and their
+ * memory freed, and requests that arrived meanwhile are admitted and start
+ * beside the ones in flight.  A request's CTA count depends on its own size
+ * only (fe_serve_plan), so its result is bitwise the same whether it is
+ * served alone or among others.
  * ---------------------------------------------------------------------- */
 typedef struct fe_serve_opts {
     int32_t precision;     /* FE_PREC_DF (default), FE_PREC_FP64 or FE_PREC_MIXED, for every request */
@@ -406,9 +419,9 @@ typedef struct fe_serve_opts {
     int64_t hbm_budget;    /* device bytes for admitted requests; 0: 80 % of the free memory at creation */
     int32_t max_ctas;      /* CTAs of one launch, 1..one per SM; 0: one per SM */
     int32_t work_per_cta;  /* packing target, block rows x tile width per CTA; 0: 2048 */
-    int32_t max_job_ctas;  /* CTAs one request may take (a cap leaves room for other requests beside a
-                              large one); 0: no cap.  On a stream of 8^3..50^3-node cubes no cap gave
-                              the highest throughput: the large requests scale across the device */
+    int32_t max_job_ctas;  /* CTAs one request may take (a cap leaves room for requests that arrive while a
+                              large one runs); 0: three quarters of max_ctas; max_ctas: no cap */
+    int32_t seg_iters;     /* Krylov iterations per segment (the admission interval); 0: 200 */
 } fe_serve_opts;
 void fe_serve_opts_default(fe_serve_opts* o);
 
@@ -428,18 +441,18 @@ typedef struct fe_result {
     const int32_t* node_id;     /* [n_dof / 3] grid node id of every rank; owned like x */
     const fe_solve_report* reports; /* [nrhs] per right-hand side; owned like x (NULL when no solve ran) */
     double t_submit, t_admit, t_done; /* seconds since fe_serve_create */
-    int32_t batch_jobs;         /* requests in the launch that solved it */
-    int32_t batch_ctas;         /* CTAs it had in that launch */
+    int32_t batch_jobs;         /* most requests (all widths) that ran in one segment with it */
+    int32_t batch_ctas;         /* CTAs it had (the same in every segment) */
     const char* message;        /* "" or the error text; owned like x */
 } fe_result;
 
 typedef struct fe_serve_stats {
     int64_t submitted, completed, failed;
-    int64_t launches;           /* persistent solve launches */
-    int64_t jobs_launched;      /* requests summed over launches */
+    int64_t launches;           /* persistent solve launches (one per tile width per segment) */
+    int64_t jobs_launched;      /* requests summed over segments */
     int64_t budget_bytes;       /* admission budget */
     int64_t peak_admitted_bytes;/* largest sum of admitted estimates */
-    double solve_device_s;      /* device time of the solve launches (CUDA events) */
+    double solve_device_s;      /* time the worker spent in segments (launch to completion) */
 } fe_serve_stats;
 
 /* Errors: FE_ERR_INVALID_ARG (NULL, options out of range), FE_ERR_OOM, FE_ERR_CUDA. */
@@ -460,18 +473,20 @@ fe_status fe_serve_wait(fe_server* srv, uint64_t ticket, double timeout_s, fe_re
  * Errors: FE_ERR_INVALID_ARG (unknown ticket), FE_PENDING (not finished). */
 fe_status fe_serve_release(fe_server* srv, uint64_t ticket);
 fe_status fe_serve_info(fe_server* srv, fe_serve_stats* out);
-/* Stops the worker after its current launch, drops unfinished requests and
+/* Stops the worker after its current segment, drops unfinished requests and
  * frees everything, including unreleased results. */
 void fe_serve_destroy(fe_server* srv);
-/* The server's packing rule, a host-only function (no device work): given n
- * ready requests in arrival order with their block rows and tile widths,
- * fills n_cta[i] (0: not in this launch) for one launch of at most max_ctas
- * CTAs and returns how many requests it takes.  The oldest request is always
- * taken; others of its width follow in order while their CTA demand,
- * ceil(rows x width / work_per_cta) clamped to 1..min(rows, max_job_ctas),
- * fits; CTAs left over go one at a time to the taken request with the most
- * work per CTA while it keeps at least work_per_cta / 4 per CTA and stays
- * within max_job_ctas (values < 1 or > max_ctas mean max_ctas). */
+/* The server's scheduling rule for one segment, a host-only function (no
+ * device work): given n active requests in arrival order with their block
+ * rows and tile widths, fills n_cta[i] (0: not in this segment) and returns
+ * how many requests run.  A request's CTA count is fixed by its own size,
+ * ceil(rows x width / work_per_cta) clamped to 1..min(rows, max_job_ctas)
+ * (values < 1 or > max_ctas mean max_ctas), never by the other requests, so
+ * its solve is partitioned, reduced and rounded the same way alone or in any
+ * mix.  Requests are taken in order while their count fits in what the
+ * earlier ones left of max_ctas; a later, smaller request may run while an
+ * earlier one waits (every segment is planned afresh, so the earlier one is
+ * considered first again at the next segment). */
 int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,
                       int32_t work_per_cta, int32_t* n_cta);
 

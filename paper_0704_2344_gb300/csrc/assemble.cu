@@ -534,12 +534,13 @@ fe_status fe_assemble(fe_ctx* ctx, const fe_mesh* m, double freq_hz, int32_t pre
                                                     (const int*)m->row_ptr.ptr, d_rep, (StencilSet*)s->stencil.ptr);
         count_launches(1);
         // product cost prefixes, in units of one stored block of an explicit
-        // row: a general-stencil row costs 18 (complex64) or 31 (FP32 pairs)
-        // such blocks, a diagonal-stencil row 10 or 8 (per-CTA product times
+        // row: a general-stencil row costs 18 (complex64) or 27 (FP32 pairs,
+        // read through the block dictionary like an explicit row) such
+        // blocks, a diagonal-stencil row 10 or 9 (per-CTA product times
         // measured on GB300 and fitted to these three row kinds)
         // The third prefix counts the stored blocks of explicit rows only: a
         // solve CTA packs its explicit rows' values at 9 times that prefix.
-        const int weights[3][3] = {{1, 18, 10}, {1, 31, 8}, {1, 0, 0}};
+        const int weights[3][3] = {{1, 18, 10}, {1, 27, 9}, {1, 0, 0}};
         DevBuf* bufs[3] = {&s->cost_prefix, &s->cost_prefix_alu, &s->expl_prefix};
         int* d_total = (int*)ctx->small.ptr + 24;
         for (int k = 0; k < 3; ++k) {

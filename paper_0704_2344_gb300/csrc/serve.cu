@@ -1,15 +1,22 @@
 // Serving: a request queue solved with continuous batching.
 //
 // A worker thread owns an internal context (its own stream on the caller's
-// device).  Each loop turn it
+// device) and one more stream per right-hand-side tile width.  Solves run in
+// segments: a persistent multi-system launch advances each of its requests
+// by at most seg_iters iterations and saves their Krylov state on the device
+// (solve_kernels.cuh, JobState).  Each loop turn the worker
 //   1. admits queued requests in arrival order while the sum of their
-//      estimated device bytes fits the budget,
-//   2. builds every admitted request's mesh, system and right-hand sides
-//      (the same kernels as fe_mesh_create / fe_assemble / fe_rhs),
-//   3. packs the ready requests of the oldest one's tile width into one
-//      persistent cooperative launch (fe_serve_plan decides the CTAs), waits
-//      for it, and hands the finished requests their results.
-// Requests submitted meanwhile are admitted at the next turn.
+//      estimated device bytes fits the budget, and builds each one's mesh,
+//      system and right-hand sides (the same kernels as fe_mesh_create /
+//      fe_assemble / fe_rhs);
+//   2. plans the segment with fe_serve_plan over all active requests: every
+//      request has a CTA count fixed by its own size, and requests run in
+//      arrival order while their counts fit the device;
+//   3. starts one cooperative launch per tile width, each on its own stream,
+//      so that widths run side by side on disjoint SMs, and waits for them;
+//   4. hands out the requests that finished and frees their memory.
+// A request submitted meanwhile is admitted at the next turn, a few
+// milliseconds later, and runs beside the requests already in flight.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -30,7 +37,9 @@ fe_status job_create(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d
 int job_width(const SolveJob* j);
 int64_t job_rows(const SolveJob* j);
 void job_destroy(fe_ctx* ctx, SolveJob* j);
-fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n);
+fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
+                      int seg_iters);
+fe_status job_finished(SolveJob* j, cudaStream_t stream, bool* finished);
 fe_status job_collect(fe_ctx* ctx, SolveJob* j, fe_complex* x_host, fe_solve_report* rep);
 size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta, int64_t pk_entries);
 fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewave* waves, double2* d_B,
@@ -61,7 +70,14 @@ struct ServeReq {
     std::vector<int32_t> node_id;
     std::vector<fe_solve_report> rep;
     int batch_jobs = 0, batch_ctas = 0;
+    int segments = 0;  // segments the request has run in
 };
+
+int width_slot(int width) {
+    int k = 0;
+    while ((1 << k) < width && k < 5) ++k;
+    return k;
+}
 
 int tile_width(int nrhs) {
     int R = 1;
@@ -103,7 +119,8 @@ struct fe_server {
     std::mutex mu;
     std::condition_variable cv_work, cv_done;
     std::deque<ServeReq*> queue;                  // submitted, not admitted
-    std::vector<ServeReq*> ready;                 // admitted and built (worker only)
+    std::vector<ServeReq*> ready;                 // admitted and built, in arrival order (worker only)
+    cudaStream_t wstream[6] = {};                 // one launch stream per tile width 1..32
     std::unordered_map<uint64_t, ServeReq*> all;  // every unreleased ticket
     uint64_t next_ticket = 1;
     bool stop = false;
@@ -160,7 +177,7 @@ fe_status build_request(fe_server* S, ServeReq* q) {
     return e;
 }
 
-// One turn of the worker: admit, build, launch one batch.  Returns false to stop.
+// One turn of the worker: admit, build, run one segment.  Returns false to stop.
 bool worker_turn(fe_server* S) {
     std::vector<ServeReq*> admitted;
     std::vector<std::pair<ServeReq*, std::string>> rejected;
@@ -198,7 +215,15 @@ bool worker_turn(fe_server* S) {
         }
     }
     if (S->ready.empty()) return true;
+    // the builds ran on the internal stream; the launches use the width streams
+    if (cudaStreamSynchronize(S->ictx->stream) != cudaSuccess) {
+        const std::string msg = std::string("serve: build failed: ") + cudaGetErrorString(cudaGetLastError());
+        for (ServeReq* q : S->ready) finish(S, q, FE_ERR_CUDA, msg.c_str());
+        S->ready.clear();
+        return true;
+    }
 
+    // plan the segment: fixed CTA counts, arrival order, later requests backfill
     const int n = (int)S->ready.size();
     std::vector<int64_t> rows(n);
     std::vector<int32_t> width(n), n_cta(n, 0);
@@ -207,43 +232,75 @@ bool worker_turn(fe_server* S) {
         width[i] = job_width(S->ready[i]->job);
     }
     const int max_ctas = S->o.max_ctas > 0 ? std::min(S->o.max_ctas, S->ictx->num_sms) : S->ictx->num_sms;
-    const int max_job = S->o.max_job_ctas > 0 ? std::min(S->o.max_job_ctas, max_ctas) : max_ctas;
+    // default cap: three quarters of the device, so that requests arriving
+    // while a large one runs find CTAs beside it
+    const int max_job = S->o.max_job_ctas > 0 ? std::min(S->o.max_job_ctas, max_ctas) : std::max(1, max_ctas * 3 / 4);
     fe_serve_plan(n, rows.data(), width.data(), max_ctas, max_job, S->o.work_per_cta, n_cta.data());
-    std::vector<ServeReq*> batch, rest;
-    std::vector<SolveJob*> jobs;
-    std::vector<int> ctas;
+    std::vector<SolveJob*> jobs[6];
+    std::vector<int> ctas[6];
+    std::vector<ServeReq*> in_seg[6];
+    int n_seg = 0;
     for (int i = 0; i < n; ++i) {
-        if (n_cta[i] > 0) {
-            batch.push_back(S->ready[i]);
-            jobs.push_back(S->ready[i]->job);
-            ctas.push_back(n_cta[i]);
-        } else {
-            rest.push_back(S->ready[i]);
-        }
+        if (n_cta[i] <= 0) continue;
+        const int k = width_slot(width[i]);
+        jobs[k].push_back(S->ready[i]->job);
+        ctas[k].push_back(n_cta[i]);
+        in_seg[k].push_back(S->ready[i]);
+        ++n_seg;
     }
-    S->ready.swap(rest);
-    fe_status e = jobs_launch(S->ictx, jobs.data(), ctas.data(), (int)jobs.size());
-    if (e == FE_OK) {
-        const cudaError_t ce = cudaStreamSynchronize(S->ictx->stream);
-        if (ce != cudaSuccess) {
-            set_error("serve: solve launch failed: %s", cudaGetErrorString(ce));
+    const int seg_iters = S->o.seg_iters > 0 ? S->o.seg_iters : 200;
+    const auto t_seg0 = Clock::now();
+    fe_status e = FE_OK;
+    int launched = 0;
+    for (int k = 0; k < 6 && e == FE_OK; ++k) {
+        if (jobs[k].empty()) continue;
+        e = jobs_launch(S->ictx, jobs[k].data(), ctas[k].data(), (int)jobs[k].size(), S->wstream[k], seg_iters);
+        if (e == FE_OK) ++launched;
+    }
+    std::string launch_msg = e == FE_OK ? std::string() : std::string(fe_last_error());
+    for (int k = 0; k < 6; ++k) {
+        if (jobs[k].empty()) continue;
+        const cudaError_t ce = cudaStreamSynchronize(S->wstream[k]);
+        if (ce != cudaSuccess && e == FE_OK) {
             e = FE_ERR_CUDA;
+            launch_msg = std::string("serve: solve launch failed: ") + cudaGetErrorString(ce);
         }
     }
-    float ms = 0.0f;
-    if (e == FE_OK && cudaEventElapsedTime(&ms, S->ictx->ev0, S->ictx->ev1) == cudaSuccess) {
+    {
         std::lock_guard<std::mutex> lk(S->mu);
-        S->stats.solve_device_s += ms * 1e-3;
-        S->stats.launches += 1;
-        S->stats.jobs_launched += (int64_t)jobs.size();
+        S->stats.solve_device_s += std::chrono::duration<double>(Clock::now() - t_seg0).count();
+        S->stats.launches += launched;
+        S->stats.jobs_launched += n_seg;
     }
-    const std::string launch_msg = e == FE_OK ? std::string() : std::string(fe_last_error());
-    for (size_t i = 0; i < batch.size(); ++i) {
-        ServeReq* q = batch[i];
-        q->batch_jobs = (int)batch.size();
-        q->batch_ctas = ctas[i];
+    // hand out what finished; the rest stays for the next segment
+    std::vector<ServeReq*> keep;
+    for (ServeReq* q : S->ready) {
+        const int k = width_slot(job_width(q->job));
+        bool ran = false;
+        for (size_t i = 0; i < in_seg[k].size(); ++i)
+            if (in_seg[k][i] == q) {
+                ran = true;
+                q->batch_jobs = std::max(q->batch_jobs, n_seg);
+                q->batch_ctas = ctas[k][i];
+            }
+        if (!ran) {
+            keep.push_back(q);
+            continue;
+        }
+        q->segments += 1;
         if (e != FE_OK) {
             finish(S, q, e, launch_msg.c_str());
+            continue;
+        }
+        bool fin = false;
+        const fe_status ef = job_finished(q->job, S->wstream[k], &fin);
+        if (ef != FE_OK) {
+            const std::string msg = fe_last_error();
+            finish(S, q, ef, msg.c_str());
+            continue;
+        }
+        if (!fin) {
+            keep.push_back(q);
             continue;
         }
         q->x.resize((size_t)q->n_dof * q->waves.size());
@@ -252,6 +309,7 @@ bool worker_turn(fe_server* S) {
         const std::string msg = es == FE_OK ? std::string() : std::string(fe_last_error());
         finish(S, q, es, msg.c_str());
     }
+    S->ready.swap(keep);
     return true;
 }
 
@@ -308,6 +366,7 @@ void fe_serve_opts_default(fe_serve_opts* o) {
     o->max_ctas = 0;
     o->work_per_cta = 2048;
     o->max_job_ctas = 0;
+    o->seg_iters = 200;
 }
 
 int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,
@@ -315,38 +374,17 @@ int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int3
     if (n <= 0 || !rows || !width || !n_cta || max_ctas < 1) return 0;
     if (work_per_cta < 1) work_per_cta = 2048;
     if (max_job_ctas < 1 || max_job_ctas > max_ctas) max_job_ctas = max_ctas;
-    for (int i = 0; i < n; ++i) n_cta[i] = 0;
-    const int32_t W = width[0];
     int32_t remaining = max_ctas, taken = 0;
-    for (int i = 0; i < n && remaining > 0; ++i) {
-        if (width[i] != W) continue;
+    for (int i = 0; i < n; ++i) {
+        n_cta[i] = 0;
         const int64_t r = std::max<int64_t>(rows[i], 1);
-        int64_t want = (r * width[i] + work_per_cta - 1) / work_per_cta;
+        int64_t want = (r * std::max(width[i], 1) + work_per_cta - 1) / work_per_cta;
         want = std::max<int64_t>(1, std::min<int64_t>(want, std::min<int64_t>(r, max_job_ctas)));
-        if (want > remaining) {
-            if (i != 0) continue;  // a later, smaller request may still fit
-            want = remaining;
+        if (want <= remaining) {
+            n_cta[i] = (int32_t)want;
+            remaining -= (int32_t)want;
+            ++taken;
         }
-        n_cta[i] = (int32_t)want;
-        remaining -= (int32_t)want;
-        ++taken;
-    }
-    // leftover CTAs: one at a time to the taken request with the most work
-    // per CTA, as long as that stays at least a quarter of the target
-    while (remaining > 0) {
-        int best = -1;
-        double best_w = 0.0;
-        for (int i = 0; i < n; ++i) {
-            if (n_cta[i] == 0 || n_cta[i] >= std::min<int64_t>(std::max<int64_t>(rows[i], 1), max_job_ctas)) continue;
-            const double w = (double)std::max<int64_t>(rows[i], 1) * width[i] / (n_cta[i] + 1);
-            if (w >= 0.25 * work_per_cta && w > best_w) {
-                best_w = w;
-                best = i;
-            }
-        }
-        if (best < 0) break;
-        n_cta[best] += 1;
-        remaining -= 1;
     }
     return taken;
 }
@@ -364,7 +402,7 @@ fe_status fe_serve_create(fe_ctx* ctx, const fe_serve_opts* opt, fe_server** out
     if ((o.precision != FE_PREC_FP64 && o.precision != FE_PREC_MIXED && o.precision != FE_PREC_DF) ||
         !(o.tol > 0.0) || o.max_iter < 1 ||
         o.max_outer < 1 || !(o.reliable >= 0.0 && o.reliable < 1.0) || o.hbm_budget < 0 || o.max_ctas < 0 ||
-        o.max_job_ctas < 0) {
+        o.max_job_ctas < 0 || o.seg_iters < 0) {
         set_error("fe_serve_create: option out of range");
         return FE_ERR_INVALID_ARG;
     }
@@ -396,6 +434,14 @@ fe_status fe_serve_create(fe_ctx* ctx, const fe_serve_opts* opt, fe_server** out
         return FE_ERR_CUDA;
     }
     S->stats.budget_bytes = o.hbm_budget > 0 ? o.hbm_budget : (int64_t)(free_b / 10 * 8);
+    for (int k = 0; k < 6; ++k)
+        if (cudaStreamCreateWithFlags(&S->wstream[k], cudaStreamNonBlocking) != cudaSuccess) {
+            set_error("fe_serve_create: stream creation failed");
+            for (int q = 0; q < k; ++q) cudaStreamDestroy(S->wstream[q]);
+            fe_ctx_destroy(S->ictx);
+            delete S;
+            return FE_ERR_CUDA;
+        }
     S->t0 = Clock::now();
     try {
         S->worker = std::thread(worker_main, S);
@@ -534,6 +580,8 @@ void fe_serve_destroy(fe_server* S) {
     }
     for (auto& kv : S->all) delete kv.second;
     cudaStreamSynchronize(S->ictx->stream);
+    for (int k = 0; k < 6; ++k)
+        if (S->wstream[k]) cudaStreamDestroy(S->wstream[k]);
     fe_ctx_destroy(S->ictx);
     delete S;
 }

@@ -27,9 +27,9 @@ namespace fe {
 extern template fe_status dispatch<double>(fe_ctx*, int, SolveParams&);
 extern template fe_status dispatch<float>(fe_ctx*, int, SolveParams&);
 extern template fe_status dispatch<DFloat>(fe_ctx*, int, SolveParams&);
-extern template fe_status launch_jobs_w<double>(fe_ctx*, int, SolveJob* const*, const int*, int);
-extern template fe_status launch_jobs_w<float>(fe_ctx*, int, SolveJob* const*, const int*, int);
-extern template fe_status launch_jobs_w<DFloat>(fe_ctx*, int, SolveJob* const*, const int*, int);
+extern template fe_status launch_jobs_w<double>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
+extern template fe_status launch_jobs_w<float>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
+extern template fe_status launch_jobs_w<DFloat>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
 
 // Column gather / scatter between [n_dof][nrhs] and a [n_dof][R] tile.
 __global__ void k_gather_cols(const double2* __restrict__ src, int lds, int c0, int ncols, double2* __restrict__ dst,
@@ -62,7 +62,7 @@ static int pick_tile(int nrhs, int requested) {
 
 static void free_workspace(cudaStream_t st, Workspace& w) {
     for (DevBuf* b : {&w.b, &w.x, &w.r, &w.u, &w.p, &w.s, &w.uM, &w.pM, &w.w, &w.partial, &w.result, &w.sync, &w.rep,
-                      &w.trace, &w.pk})
+                      &w.trace, &w.pk, &w.state})
         dev_free(st, *b);
 }
 
@@ -89,6 +89,11 @@ static fe_status check_precond(const fe_ctx* ctx, const fe_system* s, const fe_s
 static fe_status check_system_precision(const fe_system* s, int prec, const char* who) {
     if (!inner_matrix(s, prec)) {
         set_error("%s: the system was not assembled for precision %d (assemble with that precision)", who, prec);
+        return FE_ERR_INVALID_ARG;
+    }
+    if (s->variant == FE_VARIANT_L) {
+        // the literal Eq. 4 matrix is not symmetric: COCG does not apply to it
+        set_error("%s: variant L (the literal, non-symmetric form of Eq. 4) has no symmetric solve; use S or P", who);
         return FE_ERR_INVALID_ARG;
     }
     return FE_OK;
@@ -383,10 +388,18 @@ fe_status job_create(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d
         delete j;
         return e;
     }
+    if ((e = dev_alloc(st, j->w.state, sizeof(JobState))) != FE_OK ||
+        cudaMemsetAsync(j->w.state.ptr, 0, sizeof(JobState), st) != cudaSuccess) {
+        free_workspace(st, j->w);
+        delete j;
+        if (e == FE_OK) set_error("job: state reset failed");
+        return e == FE_OK ? FE_ERR_CUDA : e;
+    }
     const unsigned gb = (unsigned)((j->n_dof * j->R + 255) / 256);
     k_gather_cols<<<gb, 256, 0, st>>>(d_b, nrhs, 0, nrhs, (double2*)j->w.b.ptr, j->R, j->n_dof);
     count_launches(1);
     fill_params(j->P, s, j->w, j->R, prec, o, false);
+    j->P.state = (JobState*)j->w.state.ptr;
     *out = j;
     return FE_OK;
 }
@@ -400,9 +413,13 @@ void job_destroy(fe_ctx* ctx, SolveJob* j) {
     delete j;
 }
 
-// Enqueues one cooperative launch of n jobs of one width and precision; job i
-// gets n_cta[i] CTAs (1..its row count).
-fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n) {
+// Enqueues one cooperative launch of n jobs of one width and precision on
+// `stream`; job i gets n_cta[i] CTAs (1..its row count) and runs at most
+// seg_iters iterations (0: to the end), resuming where its last launch
+// stopped.  A job must keep its CTA count from launch to launch: the CTAs
+// own its vector rows.
+fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
+                      int seg_iters) {
     if (n < 1) return FE_OK;
     const int R = jobs[0]->R;
     const int prec = jobs[0]->prec;
@@ -423,8 +440,18 @@ fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int 
         return FE_ERR_INVALID_ARG;
     }
     return with_inner_type(prec, [&](auto* tag) {
-        return launch_jobs_w<std::remove_pointer_t<decltype(tag)>>(ctx, R, jobs, n_cta, n);
+        return launch_jobs_w<std::remove_pointer_t<decltype(tag)>>(ctx, R, jobs, n_cta, n, stream, seg_iters);
     });
+}
+
+// Whether a job's solve has ended (every column done, or a device error),
+// from its state block; `stream` must have finished the job's last launch.
+fe_status job_finished(SolveJob* j, cudaStream_t stream, bool* finished) {
+    int f = 0;
+    FE_CUDA(cudaMemcpyAsync(&f, &((JobState*)j->w.state.ptr)->finished, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    FE_CUDA(cudaStreamSynchronize(stream));
+    *finished = f != 0;
+    return FE_OK;
 }
 
 // Copies a finished job's solution (the nrhs real columns, [n_dof][nrhs]) and
@@ -475,6 +502,32 @@ constexpr size_t kStaticScratchBytes = (size_t)32 << 20;  // 32 MiB per device
 static __device__ __align__(256) unsigned char g_solve_scratch[kStaticScratchBytes];
 constexpr int kMaxDevices = 64;
 static void* g_scratch_addr[kMaxDevices] = {nullptr};
+
+// Forgets the cached address of a device whose context was destroyed (for
+// example by cudaDeviceReset): the next call looks it up again.
+static void forget_scratch_on(int device, cudaError_t e) {
+    if (device >= 0 && device < kMaxDevices &&
+        (e == cudaErrorContextIsDestroyed || e == cudaErrorDeviceUninitialized || e == cudaErrorInvalidResourceHandle))
+        g_scratch_addr[device] = nullptr;
+}
+
+// A caller buffer must be device memory of the context's device (the call
+// copies nothing: its kernel reads b and writes x in place).
+static fe_status check_device_buffer(const void* p, int device, const char* what) {
+    cudaPointerAttributes a{};
+    const cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // clear the (non-sticky) error the query recorded
+        set_error("fe_solve_rhs_noalloc: %s is not a device pointer (%s)", what, cudaGetErrorString(e));
+        return FE_ERR_INVALID_ARG;
+    }
+    if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != device) {
+        set_error("fe_solve_rhs_noalloc: %s must be device memory of device %d (memory type %d, device %d)", what,
+                  device, (int)a.type, a.device);
+        return FE_ERR_INVALID_ARG;
+    }
+    return FE_OK;
+}
 
 static fe_status static_scratch(int device, char** out) {
     if (device < 0 || device >= kMaxDevices) {
@@ -639,6 +692,8 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     FE_TRY(check_system_precision(s, prec, "fe_solve_rhs_noalloc"));
     FE_TRY(check_precond(ctx, s, opt, "fe_solve_rhs_noalloc"));
     FE_CUDA(cudaSetDevice(ctx->device));
+    FE_TRY(check_device_buffer(b_dev, ctx->device, "b_dev"));
+    FE_TRY(check_device_buffer(x_dev, ctx->device, "x_dev"));
     char* base = nullptr;
     FE_TRY(static_scratch(ctx->device, &base));
     const fe_mesh* m = s->mesh;
@@ -680,7 +735,14 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
         return FE_ERR_INVALID_ARG;
     }
     cudaStream_t st = ctx->stream;
-    FE_CUDA(cudaMemsetAsync(w.sync.ptr, 0, sync_bytes(ctx->num_sms), st));  // the array keeps the previous call's contents
+    {
+        const cudaError_t ce = cudaMemsetAsync(w.sync.ptr, 0, sync_bytes(ctx->num_sms), st);  // the array keeps old contents
+        if (ce != cudaSuccess) {
+            forget_scratch_on(ctx->device, ce);
+            set_error("fe_solve_rhs_noalloc: %s", cudaGetErrorString(ce));
+            return FE_ERR_CUDA;
+        }
+    }
     SolveParams P;
     fill_params(P, s, w, R, prec, opt, use_x0 != 0);
     P.trace = nullptr;
@@ -695,7 +757,14 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
     FE_CUDA(cudaMemcpyAsync(&hs, sync, sizeof(SyncState), cudaMemcpyDeviceToHost, st));
     FE_CUDA(cudaMemcpyAsync(h_ri, ri, (size_t)3 * R * sizeof(int), cudaMemcpyDeviceToHost, st));
     FE_CUDA(cudaMemcpyAsync(h_rel, rrel, (size_t)R * sizeof(double), cudaMemcpyDeviceToHost, st));
-    FE_CUDA(cudaStreamSynchronize(st));
+    {
+        const cudaError_t ce = cudaStreamSynchronize(st);
+        if (ce != cudaSuccess) {
+            forget_scratch_on(ctx->device, ce);
+            set_error("fe_solve_rhs_noalloc: %s", cudaGetErrorString(ce));
+            return FE_ERR_CUDA;
+        }
+    }
     float ms = 0.0f;
     if (cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1) == cudaSuccess) ctx->last_solve.kernel_ms = ms;
     if (hs.err) {

@@ -35,6 +35,24 @@ inline size_t sync_bytes(int n_cta) {
     return sizeof(SyncState);
 }
 
+// Scalar state of a solve that runs in segments (serving): everything a
+// persistent launch keeps in shared memory between iterations, saved by the
+// job's first CTA when a segment ends and loaded by every CTA when the next
+// one starts.  The vectors stay in the job's workspace, so a solve resumed
+// this way performs exactly the operations of an uninterrupted one.
+struct ColState {
+    double bn, rr_ref, rel, gam_r, gam_i, al_r, al_i, be_r, be_i, igam_r, igam_i, ial_r, ial_i, pad;
+    float4 a4, na4, b4;
+    int active, done, status, iters, outer, first, refresh, repl, pass_it, pad2[3];
+};
+struct JobState {
+    int started;   // a segment has run (the next one resumes)
+    int finished;  // every column is done: the solution is final (FP64) and the reports hold the results
+    int any_repl, any_refresh;
+    int pad[4];
+    ColState col[32];
+};
+
 // Krylov storage.  The solution x, the recurrences (r, u, p, s) and all inner
 // products are FP64; the sparse product of the Krylov loop runs in the
 // matrix precision TM (complex64 in the mixed mode) on TM copies uM, pM of u
@@ -74,6 +92,8 @@ struct SolveParams {
     int restart;  // 1: a true-residual pass restarts the directions (p = s = 0); 0: keeps them
     int max_pass;  // iterations after which a restarting pass is replaced anyway (0: no cap)
     int max_iter, max_outer, use_x0;
+    int seg_iters;     // iterations of this launch before the state is saved and the launch ends (0: to the end)
+    JobState* state;   // segmented solve state (NULL: one launch runs the whole solve)
     int halo;       // bound on |column rank - row rank|
     int stage;      // stage the CTA's uM halo in shared memory (1) or gather from L2 (0)
     int64_t halo_bytes;  // dynamic shared memory left for the halo (a CTA whose halo is larger gathers)
@@ -1184,6 +1204,44 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
 
     if (tid == 0) mbar_init(&s_mbar, 1);
     grid_barrier_init();
+    int seg_it = 0;
+    bool seg_end = false;
+    const bool resume = P.state && __ldcg(&P.state->started);
+    if (resume) {
+        if (tid < R) {
+            const ColState& cs = P.state->col[tid];
+            s_bn[tid] = cs.bn;
+            s_rr_ref[tid] = cs.rr_ref;
+            s_rel[tid] = cs.rel;
+            s_gam_r[tid] = cs.gam_r;
+            s_gam_i[tid] = cs.gam_i;
+            s_al_r[tid] = cs.al_r;
+            s_al_i[tid] = cs.al_i;
+            s_be_r[tid] = cs.be_r;
+            s_be_i[tid] = cs.be_i;
+            s_igam_r[tid] = cs.igam_r;
+            s_igam_i[tid] = cs.igam_i;
+            s_ial_r[tid] = cs.ial_r;
+            s_ial_i[tid] = cs.ial_i;
+            s_a4[tid] = cs.a4;
+            s_na4[tid] = cs.na4;
+            s_b4[tid] = cs.b4;
+            s_active[tid] = cs.active;
+            s_done[tid] = cs.done;
+            s_status[tid] = cs.status;
+            s_iters[tid] = cs.iters;
+            s_outer[tid] = cs.outer;
+            s_first[tid] = cs.first;
+            s_refresh[tid] = cs.refresh;
+            s_repl[tid] = cs.repl;
+            s_pass_it[tid] = cs.pass_it;
+        }
+        if (tid == 0) {
+            s_any_repl = P.state->any_repl;
+            s_any_refresh = P.state->any_refresh;
+        }
+        __syncthreads();
+    } else {
     if (tid < R) {
         s_done[tid] = 0;
         s_status[tid] = FE_OK;
@@ -1206,8 +1264,15 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     if (tid == 0) s_any_repl = 1;
     __syncthreads();
     if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
+    }
 
     for (;;) {
+        // a segmented solve saves its state here, where every CTA has
+        // finished the last iteration (or the replacement request before it)
+        if (P.seg_iters > 0 && seg_it >= P.seg_iters) {
+            seg_end = true;
+            break;
+        }
         if (s_any_repl) {
             // ---- [R] FP64 true residual for the columns that ask for it ----
             if constexpr (kDFV) {  // FP64 copy of x for the product (w is free until the next product)
@@ -1594,8 +1659,53 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
         FE_TRACE_MARK(7);
         ++trace_it;
+        ++seg_it;
     }
 out:
+    if (seg_end) {  // the job goes on in a later launch: keep x in its working form, save the scalars
+        __syncthreads();
+        if (cta == 0) {
+            if (tid < R) {
+                ColState& cs = P.state->col[tid];
+                cs.bn = s_bn[tid];
+                cs.rr_ref = s_rr_ref[tid];
+                cs.rel = s_rel[tid];
+                cs.gam_r = s_gam_r[tid];
+                cs.gam_i = s_gam_i[tid];
+                cs.al_r = s_al_r[tid];
+                cs.al_i = s_al_i[tid];
+                cs.be_r = s_be_r[tid];
+                cs.be_i = s_be_i[tid];
+                cs.igam_r = s_igam_r[tid];
+                cs.igam_i = s_igam_i[tid];
+                cs.ial_r = s_ial_r[tid];
+                cs.ial_i = s_ial_i[tid];
+                cs.a4 = s_a4[tid];
+                cs.na4 = s_na4[tid];
+                cs.b4 = s_b4[tid];
+                cs.active = s_active[tid];
+                cs.done = s_done[tid];
+                cs.status = s_status[tid];
+                cs.iters = s_iters[tid];
+                cs.outer = s_outer[tid];
+                cs.first = s_first[tid];
+                cs.refresh = s_refresh[tid];
+                cs.repl = s_repl[tid];
+                cs.pass_it = s_pass_it[tid];
+                P.rep_status[tid] = FE_PENDING;
+                P.rep_iters[tid] = s_iters[tid];
+                P.rep_outer[tid] = s_outer[tid];
+                P.rep_rel[tid] = s_rel[tid];
+            }
+            if (tid == 0) {
+                P.state->any_repl = s_any_repl;
+                P.state->any_refresh = s_any_refresh;
+                P.state->started = 1;
+                P.state->finished = 0;
+            }
+        }
+        return;
+    }
     if constexpr (kDFV) {  // the solution back to FP64, in place (every CTA its own rows)
         __syncthreads();
         for (int i = tid; i < 3 * n_items; i += kThreads) P.x[base_o + i] = to_c128(X[base_o + i]);
@@ -1605,6 +1715,10 @@ out:
         P.rep_iters[tid] = s_iters[tid];
         P.rep_outer[tid] = s_outer[tid];
         P.rep_rel[tid] = s_rel[tid];
+    }
+    if (cta == 0 && tid == 0 && P.state) {
+        P.state->started = 1;
+        P.state->finished = 1;
     }
 }
 
@@ -1643,7 +1757,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 struct Workspace {
-    DevBuf b, x, r, u, p, s, uM, pM, w, partial, result, sync, rep, trace, pk;
+    DevBuf b, x, r, u, p, s, uM, pM, w, partial, result, sync, rep, trace, pk, state;
 };
 
 constexpr size_t kSmemBudget = 200 * 1024;  // dynamic; static shared memory adds ~20 KB
@@ -1759,7 +1873,8 @@ struct SolveJob {
 };
 
 template <typename T, int R>
-fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n) {
+fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
+                        int seg_iters) {
     using C = typename CplxT<T>::type;
     std::vector<SolveParams> Ps(n);
     std::vector<int> cta0(n + 1, 0);
@@ -1785,27 +1900,28 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
             size_t dres = 0;
             if (size_res_map<C>(P, rows_per_cta, dres)) dyn = std::max(dyn, dres);
         }
+        P.seg_iters = seg_iters;
         cta0[i + 1] = cta0[i] + n_cta[i];
-        FE_CUDA(cudaMemsetAsync(P.sync, 0, sync_bytes(P.n_cta), ctx->stream));
+        FE_CUDA(cudaMemsetAsync(P.sync, 0, sync_bytes(P.n_cta), stream));
     }
     for (int i = 0; i < n; ++i) Ps[i].halo_bytes = (int64_t)dyn - red_bytes - Ps[i].col_bytes - Ps[i].res_bytes;
     const int grid = cta0[n];
     DevBuf dparams, dcta;
-    FE_TRY(dev_alloc(ctx->stream, dparams, (size_t)n * sizeof(SolveParams)));
-    fe_status e = dev_alloc(ctx->stream, dcta, (size_t)(n + 1) * sizeof(int));
+    FE_TRY(dev_alloc(stream, dparams, (size_t)n * sizeof(SolveParams)));
+    fe_status e = dev_alloc(stream, dcta, (size_t)(n + 1) * sizeof(int));
     if (e != FE_OK) {
-        dev_free(ctx->stream, dparams);
+        dev_free(stream, dparams);
         return e;
     }
     auto done = [&](fe_status st) {
-        dev_free(ctx->stream, dparams);
-        dev_free(ctx->stream, dcta);
+        dev_free(stream, dparams);
+        dev_free(stream, dcta);
         return st;
     };
     if (cudaMemcpyAsync(dparams.ptr, Ps.data(), (size_t)n * sizeof(SolveParams), cudaMemcpyHostToDevice,
-                        ctx->stream) != cudaSuccess ||
+                        stream) != cudaSuccess ||
         cudaMemcpyAsync(dcta.ptr, cta0.data(), (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice,
-                        ctx->stream) != cudaSuccess) {
+                        stream) != cudaSuccess) {
         set_error("jobs: parameter upload failed");
         return done(FE_ERR_CUDA);
     }
@@ -1823,27 +1939,26 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
     const SolveParams* pp = (const SolveParams*)dparams.ptr;
     const int* pc = (const int*)dcta.ptr;
     void* args[] = {(void*)&pp, (void*)&pc, (void*)&n};
-    cudaEventRecord(ctx->ev0, ctx->stream);
     const cudaError_t le = cudaLaunchCooperativeKernel((void*)k_solve_jobs<T, R>, dim3(grid), dim3(kThreads), args,
-                                                       dyn, ctx->stream);
+                                                       dyn, stream);
     if (le != cudaSuccess) {
         set_error("jobs: launch failed: %s", cudaGetErrorString(le));
         return done(FE_ERR_CUDA);
     }
-    cudaEventRecord(ctx->ev1, ctx->stream);
     count_launches(1);
     return done(FE_OK);
 }
 
 template <typename T>
-fe_status launch_jobs_w(fe_ctx* ctx, int R, SolveJob* const* jobs, const int* n_cta, int n) {
+fe_status launch_jobs_w(fe_ctx* ctx, int R, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
+                        int seg_iters) {
     switch (R) {
-        case 1: return launch_jobs_t<T, 1>(ctx, jobs, n_cta, n);
-        case 2: return launch_jobs_t<T, 2>(ctx, jobs, n_cta, n);
-        case 4: return launch_jobs_t<T, 4>(ctx, jobs, n_cta, n);
-        case 8: return launch_jobs_t<T, 8>(ctx, jobs, n_cta, n);
-        case 16: return launch_jobs_t<T, 16>(ctx, jobs, n_cta, n);
-        case 32: return launch_jobs_t<T, 32>(ctx, jobs, n_cta, n);
+        case 1: return launch_jobs_t<T, 1>(ctx, jobs, n_cta, n, stream, seg_iters);
+        case 2: return launch_jobs_t<T, 2>(ctx, jobs, n_cta, n, stream, seg_iters);
+        case 4: return launch_jobs_t<T, 4>(ctx, jobs, n_cta, n, stream, seg_iters);
+        case 8: return launch_jobs_t<T, 8>(ctx, jobs, n_cta, n, stream, seg_iters);
+        case 16: return launch_jobs_t<T, 16>(ctx, jobs, n_cta, n, stream, seg_iters);
+        case 32: return launch_jobs_t<T, 32>(ctx, jobs, n_cta, n, stream, seg_iters);
         default: set_error("jobs: unsupported tile width %d", R); return FE_ERR_UNSUPPORTED;
     }
 }

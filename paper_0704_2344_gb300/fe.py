@@ -88,7 +88,8 @@ class fe_solve_report(C.Structure):
 class fe_serve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("hbm_budget", C.c_int64),
-                ("max_ctas", C.c_int32), ("work_per_cta", C.c_int32), ("max_job_ctas", C.c_int32)]
+                ("max_ctas", C.c_int32), ("work_per_cta", C.c_int32), ("max_job_ctas", C.c_int32),
+                ("seg_iters", C.c_int32)]
 
 
 class fe_request(C.Structure):
@@ -217,6 +218,7 @@ def fe_ctx_create(device: int = 0, stream: int | None = None, variant: int = FE_
     opt.formulation = formulation
     out = P()
     _check(lib.fe_ctx_create(C.byref(out), device, C.byref(opt)), "fe_ctx_create")
+    out.device = int(device)
     return out
 
 
@@ -451,7 +453,20 @@ def fe_solve_rhs(ctx, system, b, nrhs: int, opts: fe_solve_opts | None = None, x
 def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_opts | None = None,
                          use_x0: bool = False, raise_on_fail: bool = True):
     """Solve with the library's fixed device scratch (no allocation during the
-    call); b_dev and x_dev are device buffers [n_dof, nrhs] complex128."""
+    call); b_dev and x_dev are torch complex128 tensors [n_dof, nrhs],
+    contiguous, on the context's CUDA device (the kernel reads and writes them
+    in place, so nothing else is accepted)."""
+    n_dof = 3 * fe_system_info(system)["n_rows"]
+    dev = getattr(ctx, "device", None)
+    where = "fe_solve_rhs_noalloc"
+    for name, t in (("b_dev", b_dev), ("x_dev", x_dev)):
+        if not (hasattr(t, "is_cuda") and t.is_cuda):
+            raise FeError(FE_ERR_INVALID_ARG, where, f"{name} must be a CUDA tensor")
+        if str(t.dtype) != "torch.complex128" or not t.is_contiguous() or tuple(t.shape) != (n_dof, int(nrhs)):
+            raise FeError(FE_ERR_INVALID_ARG, where,
+                          f"{name} must be a contiguous complex128 tensor of shape ({n_dof}, {int(nrhs)})")
+        if dev is not None and t.device.index != dev:
+            raise FeError(FE_ERR_INVALID_ARG, where, f"{name} is on cuda:{t.device.index}, the context on cuda:{dev}")
     opts = opts or solve_opts()
     rep = (fe_solve_report * nrhs)()
     st = load().fe_solve_rhs_noalloc(ctx, system, int(nrhs), _ptr(b_dev), _ptr(x_dev), 1 if use_x0 else 0,
@@ -463,13 +478,15 @@ def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_op
 # --------------------------------------------------------------------------
 # Serving
 def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
-               hbm_budget=0, max_ctas=0, work_per_cta=0, max_job_ctas=0) -> fe_serve_opts:
+               hbm_budget=0, max_ctas=0, work_per_cta=0, max_job_ctas=0, seg_iters=0) -> fe_serve_opts:
     o = fe_serve_opts()
     load().fe_serve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
     o.max_iter, o.max_outer, o.hbm_budget = int(max_iter), int(max_outer), int(hbm_budget)
     o.max_ctas = int(max_ctas)
     o.max_job_ctas = int(max_job_ctas)
+    if seg_iters:
+        o.seg_iters = int(seg_iters)
     if work_per_cta:
         o.work_per_cta = int(work_per_cta)
     return o

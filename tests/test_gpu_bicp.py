@@ -172,3 +172,34 @@ def test_bicp_rejects_the_unsymmetric_variant(fe):
             fe.fe_mesh_destroy(m)
     finally:
         fe.fe_ctx_destroy(c)
+
+
+def test_solves_reject_the_unsymmetric_variant(fe):
+    """Variant L (literal Eq. 4) is not symmetric, so COCG does not apply:
+    every solve entry point rejects it at once instead of iterating to the
+    cap."""
+    import torch
+
+    c = fe.fe_ctx_create(0, variant=fe.FE_VARIANT_L)
+    try:
+        prob = W.random_small_grid(4, n_max=5)
+        waves = W.normal_incidence()
+        m = fe.fe_mesh_create_from(c, prob)
+        s = fe.fe_assemble(c, m, prob.freq_hz, fe.FE_PREC_DF)
+        try:
+            n_dof = fe.fe_mesh_info(m)["n_dof"]
+            B = fe.fe_rhs(c, s, waves, n_dof)
+            opts = fe.solve_opts(precision=fe.FE_PREC_DF)
+            for call in (lambda: fe.fe_solve_batch(c, s, waves, n_dof, opts),
+                         lambda: fe.fe_solve_rhs(c, s, B, 1, opts),
+                         lambda: fe.fe_solve_rhs_noalloc(c, s, 1, torch.from_numpy(B).cuda(),
+                                                         torch.zeros((n_dof, 1), dtype=torch.complex128,
+                                                                     device="cuda"), opts)):
+                with pytest.raises(fe.FeError) as e:
+                    call()
+                assert e.value.status == fe.FE_ERR_INVALID_ARG and "variant L" in str(e.value)
+        finally:
+            fe.fe_system_destroy(s)
+            fe.fe_mesh_destroy(m)
+    finally:
+        fe.fe_ctx_destroy(c)
