@@ -303,7 +303,14 @@ fe_status fe_spmv_half(fe_ctx* ctx, const fe_system* s, int32_t precision, int32
  * refreshes.  The true residual decides convergence: ||b - A x|| / ||b|| <= tol
  * for every right-hand side.  Up to
  * rhs_tile right-hand sides are solved together in one persistent device
- * launch.
+ * launch.  With rhs_tile = 0 and at least 8 right-hand sides, the first solve
+ * of a system shape (unknowns, right-hand sides, precision, variant, device)
+ * runs the autotuner: short trial launches (32 iterations of the first
+ * columns) for every tile width in {8, 16, 32} up to the column count and
+ * grids of all or three quarters of the SMs, timed with CUDA events; the
+ * fastest per column and iteration is kept for that shape in a process-wide
+ * cache and reported in fe_solve_stats.  Fewer right-hand sides use the
+ * widest power of two up to their count.
  * ---------------------------------------------------------------------- */
 typedef enum fe_preconditioner {
     FE_PRECOND_BLOCK_JACOBI = 0, /* inverse 3x3 node blocks (the diagonal preconditioning of Section
@@ -399,7 +406,7 @@ fe_status fe_solve_rhs_noalloc(fe_ctx* ctx, const fe_system* s, int32_t nrhs, co
  * caller).  The worker admits queued requests in arrival order while the
  * sum of their estimated device memory stays within the budget, and builds
  * each admitted request's mesh, system (Eqs. 1-4) and right-hand sides.
- * Solves then run in segments of seg_iters iterations: each segment is one
+ * Solves then run in segments of about 25 ms: each segment is one
  * persistent cooperative launch per right-hand-side tile width (1, 2, 4, 8,
  * 16 or 32 after padding with zero columns), the widths side by side on
  * their own streams; every request has its own range of CTAs, synchronises
@@ -421,7 +428,8 @@ typedef struct fe_serve_opts {
     int32_t work_per_cta;  /* packing target, block rows x tile width per CTA; 0: 2048 */
     int32_t max_job_ctas;  /* CTAs one request may take (a cap leaves room for requests that arrive while a
                               large one runs); 0: three quarters of max_ctas; max_ctas: no cap */
-    int32_t seg_iters;     /* Krylov iterations per segment (the admission interval); 0: 200 */
+    int32_t seg_iters;     /* Krylov iterations per segment; 0 (default): each request runs as many as fill
+                              about 25 ms at its own measured time per iteration (64 in its first segment) */
 } fe_serve_opts;
 void fe_serve_opts_default(fe_serve_opts* o);
 
@@ -500,6 +508,9 @@ typedef struct fe_solve_stats {
     int64_t passes;          /* refinement passes (true-residual evaluations), summed over tiles */
     int64_t tile_width;      /* right-hand sides per launch */
     int64_t grid_ctas;       /* CTAs of the cooperative launch */
+    int64_t tuned;           /* how tile_width and grid_ctas were chosen: 0 the fixed rule (or the caller's
+                                rhs_tile), 1 timed by the autotuner in this call, 2 the autotuner's cached choice */
+    double tune_ms;          /* device time of the autotuner's trial launches in this call */
 } fe_solve_stats;
 fe_status fe_last_solve_stats(const fe_ctx* ctx, fe_solve_stats* out);
 

@@ -38,8 +38,8 @@ int job_width(const SolveJob* j);
 int64_t job_rows(const SolveJob* j);
 void job_destroy(fe_ctx* ctx, SolveJob* j);
 fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
-                      int seg_iters);
-fe_status job_finished(SolveJob* j, cudaStream_t stream, bool* finished);
+                      const int* seg_iters);
+fe_status job_progress(SolveJob* j, cudaStream_t stream, bool* finished, int* seg_done, double* seg_ms);
 fe_status job_collect(fe_ctx* ctx, SolveJob* j, fe_complex* x_host, fe_solve_report* rep);
 size_t workspace_bytes(int64_t n_dof, int R, int prec, int max_cta, int64_t pk_entries);
 fe_status build_rhs(fe_ctx* ctx, const fe_system* s, int nrhs, const fe_planewave* waves, double2* d_B,
@@ -70,8 +70,21 @@ struct ServeReq {
     std::vector<int32_t> node_id;
     std::vector<fe_solve_report> rep;
     int batch_jobs = 0, batch_ctas = 0;
-    int segments = 0;  // segments the request has run in
+    int segments = 0;         // segments the request has run in
+    double ms_per_iter = 0.0;  // device time per iteration measured in its last segment (0: none yet)
 };
+
+// Segments last about kSegTargetMs: each request runs as many iterations as
+// its own measured time per iteration allows, so that a small request
+// launched beside a large one keeps its SMs busy for the whole segment.
+constexpr double kSegTargetMs = 25.0;
+constexpr int kSegFirst = 64;
+
+int segment_iters(const fe_serve_opts& o, const ServeReq* q) {
+    if (o.seg_iters > 0) return o.seg_iters;
+    if (!(q->ms_per_iter > 0.0)) return kSegFirst;
+    return (int)std::max(16.0, std::min(1e6, kSegTargetMs / q->ms_per_iter));
+}
 
 int width_slot(int width) {
     int k = 0;
@@ -237,7 +250,7 @@ bool worker_turn(fe_server* S) {
     const int max_job = S->o.max_job_ctas > 0 ? std::min(S->o.max_job_ctas, max_ctas) : std::max(1, max_ctas * 3 / 4);
     fe_serve_plan(n, rows.data(), width.data(), max_ctas, max_job, S->o.work_per_cta, n_cta.data());
     std::vector<SolveJob*> jobs[6];
-    std::vector<int> ctas[6];
+    std::vector<int> ctas[6], iters[6];
     std::vector<ServeReq*> in_seg[6];
     int n_seg = 0;
     for (int i = 0; i < n; ++i) {
@@ -245,16 +258,17 @@ bool worker_turn(fe_server* S) {
         const int k = width_slot(width[i]);
         jobs[k].push_back(S->ready[i]->job);
         ctas[k].push_back(n_cta[i]);
+        iters[k].push_back(segment_iters(S->o, S->ready[i]));
         in_seg[k].push_back(S->ready[i]);
         ++n_seg;
     }
-    const int seg_iters = S->o.seg_iters > 0 ? S->o.seg_iters : 200;
     const auto t_seg0 = Clock::now();
     fe_status e = FE_OK;
     int launched = 0;
     for (int k = 0; k < 6 && e == FE_OK; ++k) {
         if (jobs[k].empty()) continue;
-        e = jobs_launch(S->ictx, jobs[k].data(), ctas[k].data(), (int)jobs[k].size(), S->wstream[k], seg_iters);
+        e = jobs_launch(S->ictx, jobs[k].data(), ctas[k].data(), (int)jobs[k].size(), S->wstream[k],
+                        iters[k].data());
         if (e == FE_OK) ++launched;
     }
     std::string launch_msg = e == FE_OK ? std::string() : std::string(fe_last_error());
@@ -293,7 +307,10 @@ bool worker_turn(fe_server* S) {
             continue;
         }
         bool fin = false;
-        const fe_status ef = job_finished(q->job, S->wstream[k], &fin);
+        int done_it = 0;
+        double seg_ms = 0.0;
+        const fe_status ef = job_progress(q->job, S->wstream[k], &fin, &done_it, &seg_ms);
+        if (done_it > 0) q->ms_per_iter = seg_ms / done_it;
         if (ef != FE_OK) {
             const std::string msg = fe_last_error();
             finish(S, q, ef, msg.c_str());
@@ -366,7 +383,7 @@ void fe_serve_opts_default(fe_serve_opts* o) {
     o->max_ctas = 0;
     o->work_per_cta = 2048;
     o->max_job_ctas = 0;
-    o->seg_iters = 200;
+    o->seg_iters = 0;
 }
 
 int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,

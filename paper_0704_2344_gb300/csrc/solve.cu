@@ -17,8 +17,12 @@
 #include "krylov.cuh"
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdlib>
+#include <map>
+#include <mutex>
 #include <new>
+#include <tuple>
 #include "solve_kernels.cuh"
 
 namespace fe {
@@ -27,9 +31,9 @@ namespace fe {
 extern template fe_status dispatch<double>(fe_ctx*, int, SolveParams&);
 extern template fe_status dispatch<float>(fe_ctx*, int, SolveParams&);
 extern template fe_status dispatch<DFloat>(fe_ctx*, int, SolveParams&);
-extern template fe_status launch_jobs_w<double>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
-extern template fe_status launch_jobs_w<float>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
-extern template fe_status launch_jobs_w<DFloat>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
+extern template fe_status launch_jobs_w<double>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, const int*);
+extern template fe_status launch_jobs_w<float>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, const int*);
+extern template fe_status launch_jobs_w<DFloat>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, const int*);
 
 // Column gather / scatter between [n_dof][nrhs] and a [n_dof][R] tile.
 __global__ void k_gather_cols(const double2* __restrict__ src, int lds, int c0, int ncols, double2* __restrict__ dst,
@@ -240,16 +244,106 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     }
 }
 
+// Solves the first nrhs columns of b (leading dimension ldb) into x (same
+// leading dimension), R columns per launch.
+static fe_status solve_tiles(fe_ctx* ctx, const fe_system* s, int nrhs, int ldb, const double2* d_b, double2* d_x,
+                             bool use_x0, const fe_solve_opts& o, fe_solve_report* rep, int R, int n_cta_req);
+
+// ---------------------------------------------------------------------------
+// Autotuner of the tile width and the grid of multi-column solves.  A trial
+// is a real solve of the first columns capped at kTuneIters iterations; its
+// measure is device time per column and iteration.  Choices are cached per
+// system shape for the life of the process.
+// ---------------------------------------------------------------------------
+constexpr int kTuneIters = 32;
+
+struct TuneKey {
+    int64_t n_dof, nnzb;
+    int nrhs, prec, variant, device;
+    bool operator<(const TuneKey& o) const {
+        return std::tie(n_dof, nnzb, nrhs, prec, variant, device) <
+               std::tie(o.n_dof, o.nnzb, o.nrhs, o.prec, o.variant, o.device);
+    }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, std::pair<int, int>> g_tune;  // (tile width, CTAs)
+
+static fe_status autotune(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d_b, const fe_solve_opts& o,
+                          int* R_out, int* cta_out, int* how, double* tune_ms) {
+    const TuneKey key{3 * (int64_t)s->mesh->n_act, s->mesh->nnzb, std::min(nrhs, 32), o.precision, s->variant,
+                      ctx->device};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            *R_out = it->second.first;
+            *cta_out = it->second.second;
+            *how = 2;
+            return FE_OK;
+        }
+    }
+    const int64_t n_dof = key.n_dof;
+    const int top = pick_tile(nrhs, 0);
+    DevBuf xt;
+    FE_TRY(dev_alloc(ctx->stream, xt, (size_t)n_dof * nrhs * sizeof(double2)));
+    fe_solve_opts t = o;
+    t.max_iter = kTuneIters;
+    t.tol = 1e-300;  // trials never converge early
+    double best = 1e300;
+    int bestR = top, bestC = ctx->num_sms;
+    fe_status e = FE_OK;
+    const int grids[2] = {ctx->num_sms, std::max(1, ctx->num_sms * 3 / 4)};
+    for (int W = 8; W <= top && e == FE_OK; W *= 2)
+        for (int g = 0; g < 2 && e == FE_OK; ++g) {
+            const fe_status es = solve_tiles(ctx, s, std::min(nrhs, W), nrhs, d_b, (double2*)xt.ptr, false, t, nullptr,
+                                             W, grids[g]);
+            if (es != FE_OK && es != FE_ERR_NOT_CONVERGED && es != FE_ERR_BREAKDOWN) {
+                e = es;
+                break;
+            }
+            const fe_solve_stats& st = ctx->last_solve;
+            *tune_ms += st.kernel_ms;
+            // real columns only: the zero columns of a padded tile are done at once
+            const double per = st.inner_iters > 0 ? st.kernel_ms / (double)st.inner_iters : 1e300;
+            if (per < best) {
+                best = per;
+                bestR = W;
+                bestC = grids[g];
+            }
+        }
+    dev_free(ctx->stream, xt);
+    if (e != FE_OK) return e;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune[key] = {bestR, bestC};
+    }
+    *R_out = bestR;
+    *cta_out = bestC;
+    *how = 1;
+    return FE_OK;
+}
+
 // Solves tile by tile; b and x are device arrays [n_dof][nrhs].
 static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const double2* d_b, double2* d_x,
                               bool use_x0, const fe_solve_opts& o, fe_solve_report* rep) {
+    FE_TRY(check_system_precision(s, o.precision, "solve"));
+    FE_TRY(check_precond(ctx, s, o, "solve"));
+    int R = pick_tile(nrhs, o.rhs_tile), n_cta = 0, how = 0;
+    double tune_ms = 0.0;
+    if (o.rhs_tile == 0 && nrhs >= 8 && o.preconditioner == FE_PRECOND_BLOCK_JACOBI)
+        FE_TRY(autotune(ctx, s, nrhs, d_b, o, &R, &n_cta, &how, &tune_ms));
+    const fe_status e = solve_tiles(ctx, s, nrhs, nrhs, d_b, d_x, use_x0, o, rep, R, n_cta);
+    ctx->last_solve.tuned = how;
+    ctx->last_solve.tune_ms = tune_ms;
+    return e;
+}
+
+static fe_status solve_tiles(fe_ctx* ctx, const fe_system* s, int nrhs, int ldb, const double2* d_b, double2* d_x,
+                             bool use_x0, const fe_solve_opts& o, fe_solve_report* rep, int R, int n_cta_req) {
     const fe_mesh* m = s->mesh;
     cudaStream_t st = ctx->stream;
     const int64_t n_dof = 3 * (int64_t)m->n_act;
-    const int R = pick_tile(nrhs, o.rhs_tile);
     const int prec = o.precision;
-    FE_TRY(check_system_precision(s, prec, "solve"));
-    FE_TRY(check_precond(ctx, s, o, "solve"));
     Workspace w;
     auto cleanup = [&]() { free_workspace(st, w); };
     fe_status e = alloc_workspace(st, n_dof, R, prec, 2 * ctx->num_sms, w, packed_entries(s, prec, R));
@@ -269,20 +363,21 @@ static fe_status solve_device(fe_ctx* ctx, const fe_system* s, int nrhs, const d
     for (int c0 = 0; c0 < nrhs; c0 += R) {
         const int nc = std::min(R, nrhs - c0);
         const unsigned gb = (unsigned)((n_dof * R + 255) / 256);
-        k_gather_cols<<<gb, 256, 0, st>>>(d_b, nrhs, c0, nc, (double2*)w.b.ptr, R, n_dof);
+        k_gather_cols<<<gb, 256, 0, st>>>(d_b, ldb, c0, nc, (double2*)w.b.ptr, R, n_dof);
         count_launches(1);
         if (use_x0) {
-            k_gather_cols<<<gb, 256, 0, st>>>(d_x, nrhs, c0, nc, (double2*)w.x.ptr, R, n_dof);
+            k_gather_cols<<<gb, 256, 0, st>>>(d_x, ldb, c0, nc, (double2*)w.x.ptr, R, n_dof);
             count_launches(1);
         }
         cudaMemsetAsync(w.sync.ptr, 0, sync_bytes(ctx->num_sms), st);
         SolveParams P;
         fill_params(P, s, w, R, prec, o, use_x0);
+        P.n_cta_req = n_cta_req;
         int* ri = P.rep_status;
         e = with_inner_type(prec, [&](auto* tag) { return dispatch<std::remove_pointer_t<decltype(tag)>>(ctx, R, P); });
         if (e != FE_OK) break;
         const unsigned gs = (unsigned)((n_dof * nc + 255) / 256);
-        k_scatter_cols<<<gs, 256, 0, st>>>((const double2*)w.x.ptr, R, nc, d_x, nrhs, c0, n_dof);
+        k_scatter_cols<<<gs, 256, 0, st>>>((const double2*)w.x.ptr, R, nc, d_x, ldb, c0, n_dof);
         count_launches(1);
         SyncState hs{};
         cudaMemcpyAsync(&hs, w.sync.ptr, sizeof(SyncState), cudaMemcpyDeviceToHost, st);
@@ -415,11 +510,11 @@ void job_destroy(fe_ctx* ctx, SolveJob* j) {
 
 // Enqueues one cooperative launch of n jobs of one width and precision on
 // `stream`; job i gets n_cta[i] CTAs (1..its row count) and runs at most
-// seg_iters iterations (0: to the end), resuming where its last launch
-// stopped.  A job must keep its CTA count from launch to launch: the CTAs
+// seg_iters[i] iterations (seg_iters NULL or 0: to the end), resuming where
+// its last launch stopped.  A job must keep its CTA count from launch to launch: the CTAs
 // own its vector rows.
 fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
-                      int seg_iters) {
+                      const int* seg_iters) {
     if (n < 1) return FE_OK;
     const int R = jobs[0]->R;
     const int prec = jobs[0]->prec;
@@ -444,13 +539,21 @@ fe_status jobs_launch(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int 
     });
 }
 
-// Whether a job's solve has ended (every column done, or a device error),
-// from its state block; `stream` must have finished the job's last launch.
-fe_status job_finished(SolveJob* j, cudaStream_t stream, bool* finished) {
-    int f = 0;
-    FE_CUDA(cudaMemcpyAsync(&f, &((JobState*)j->w.state.ptr)->finished, sizeof(int), cudaMemcpyDeviceToHost, stream));
+// A job's progress after a launch, from its state block: whether the solve
+// has ended (every column done, or a device error), the iterations its last
+// segment ran and their device time.  `stream` must have finished the job's
+// last launch.
+fe_status job_progress(SolveJob* j, cudaStream_t stream, bool* finished, int* seg_done, double* seg_ms) {
+    struct {
+        int started, finished, any_repl, any_refresh, seg_done, pad[3];
+        unsigned long long seg_ns;
+    } h{};
+    static_assert(sizeof(h) == offsetof(JobState, seg_ns) + sizeof(unsigned long long), "state header layout");
+    FE_CUDA(cudaMemcpyAsync(&h, j->w.state.ptr, sizeof(h), cudaMemcpyDeviceToHost, stream));
     FE_CUDA(cudaStreamSynchronize(stream));
-    *finished = f != 0;
+    *finished = h.finished != 0;
+    *seg_done = h.seg_done;
+    *seg_ms = (double)h.seg_ns * 1e-6;
     return FE_OK;
 }
 

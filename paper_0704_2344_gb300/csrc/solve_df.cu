@@ -4,5 +4,5 @@
 
 namespace fe {
 template fe_status dispatch<DFloat>(fe_ctx*, int, SolveParams&);
-template fe_status launch_jobs_w<DFloat>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, int);
+template fe_status launch_jobs_w<DFloat>(fe_ctx*, int, SolveJob* const*, const int*, int, cudaStream_t, const int*);
 }  // namespace fe

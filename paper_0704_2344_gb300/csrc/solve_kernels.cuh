@@ -49,7 +49,9 @@ struct JobState {
     int started;   // a segment has run (the next one resumes)
     int finished;  // every column is done: the solution is final (FP64) and the reports hold the results
     int any_repl, any_refresh;
-    int pad[4];
+    int seg_done;  // iterations the last segment ran
+    int pad[3];
+    unsigned long long seg_ns;  // device time of the last segment (its first CTA, start to end)
     ColState col[32];
 };
 
@@ -93,6 +95,7 @@ struct SolveParams {
     int max_pass;  // iterations after which a restarting pass is replaced anyway (0: no cap)
     int max_iter, max_outer, use_x0;
     int seg_iters;     // iterations of this launch before the state is saved and the launch ends (0: to the end)
+    int n_cta_req;     // CTAs of a single-system launch (0: one per SM)
     JobState* state;   // segmented solve state (NULL: one launch runs the whole solve)
     int halo;       // bound on |column rank - row rank|
     int stage;      // stage the CTA's uM halo in shared memory (1) or gather from L2 (0)
@@ -1206,6 +1209,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     grid_barrier_init();
     int seg_it = 0;
     bool seg_end = false;
+    const unsigned long long seg_t0 = (P.state && cta == 0 && tid == 0) ? globaltimer_ns() : 0ull;
     const bool resume = P.state && __ldcg(&P.state->started);
     if (resume) {
         if (tid < R) {
@@ -1700,6 +1704,8 @@ out:
             if (tid == 0) {
                 P.state->any_repl = s_any_repl;
                 P.state->any_refresh = s_any_refresh;
+                P.state->seg_done = seg_it;
+                P.state->seg_ns = globaltimer_ns() - seg_t0;
                 P.state->started = 1;
                 P.state->finished = 0;
             }
@@ -1717,6 +1723,8 @@ out:
         P.rep_rel[tid] = s_rel[tid];
     }
     if (cta == 0 && tid == 0 && P.state) {
+        P.state->seg_done = seg_it;
+        P.state->seg_ns = globaltimer_ns() - seg_t0;
         P.state->started = 1;
         P.state->finished = 1;
     }
@@ -1811,7 +1819,7 @@ fe_status launch_solve(fe_ctx* ctx, SolveParams& P) {
     using C = typename CplxT<T>::type;
     // one CTA per SM; the reduction scratch and (when it fits) the CTA's
     // vector halo live in dynamic shared memory
-    P.n_cta = std::min(ctx->num_sms, std::max(1, P.n_rows));
+    P.n_cta = std::min(P.n_cta_req > 0 ? std::min(P.n_cta_req, ctx->num_sms) : ctx->num_sms, std::max(1, P.n_rows));
     P.part_half = (int64_t)P.n_cta * kMaxNV * R;
     P.red_bytes = (int)(kMaxNV * kWarps * R * sizeof(double));
     P.col_bytes = R == 1 ? (int)(kWarps * kColsPerWarp * sizeof(int)) : 0;
@@ -1874,7 +1882,7 @@ struct SolveJob {
 
 template <typename T, int R>
 fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
-                        int seg_iters) {
+                        const int* seg_iters) {
     using C = typename CplxT<T>::type;
     std::vector<SolveParams> Ps(n);
     std::vector<int> cta0(n + 1, 0);
@@ -1900,7 +1908,7 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
             size_t dres = 0;
             if (size_res_map<C>(P, rows_per_cta, dres)) dyn = std::max(dyn, dres);
         }
-        P.seg_iters = seg_iters;
+        P.seg_iters = seg_iters ? seg_iters[i] : 0;
         cta0[i + 1] = cta0[i] + n_cta[i];
         FE_CUDA(cudaMemsetAsync(P.sync, 0, sync_bytes(P.n_cta), stream));
     }
@@ -1951,7 +1959,7 @@ fe_status launch_jobs_t(fe_ctx* ctx, SolveJob* const* jobs, const int* n_cta, in
 
 template <typename T>
 fe_status launch_jobs_w(fe_ctx* ctx, int R, SolveJob* const* jobs, const int* n_cta, int n, cudaStream_t stream,
-                        int seg_iters) {
+                        const int* seg_iters) {
     switch (R) {
         case 1: return launch_jobs_t<T, 1>(ctx, jobs, n_cta, n, stream, seg_iters);
         case 2: return launch_jobs_t<T, 2>(ctx, jobs, n_cta, n, stream, seg_iters);

@@ -101,6 +101,106 @@ __global__ void __launch_bounds__(256) k_spmv_warp(const C* __restrict__ val, in
     }
 }
 
+// y = A x for R = 8, 16 or 32 columns: a warp takes G = 32/R consecutive
+// block rows, one group of R lanes (one lane per column) per row.  The warp
+// first copies the nine entries and the column index of every block of its
+// G rows into shared memory with coalesced loads (lane l takes block l, l +
+// 32, ...: the blocks of consecutive rows are consecutive in each plane), so
+// that the whole group of rows is in flight at once; then each group walks
+// its row from shared memory (the R lanes read the same entry) and multiplies
+// by the R contiguous vector values of each block's column.  No reduction
+// across lanes is needed.
+constexpr int kSpmmWarps = 4;
+
+template <typename C, int R>
+__global__ void __launch_bounds__(32 * kSpmmWarps) k_spmm_rows(const C* __restrict__ val, int64_t stride,
+                                                               const int* __restrict__ col,
+                                                               const int* __restrict__ rp, const C* __restrict__ x,
+                                                               C* __restrict__ y, int n_rows) {
+    constexpr int G = 32 / R;
+    constexpr int kMax = 27 * G;
+    __shared__ C s_val[kSpmmWarps][9][kMax];
+    __shared__ int s_col[kSpmmWarps][kMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c = lane % R, g = lane / R;
+    const int n_groups = (n_rows + G - 1) / G;
+    const int nw = gridDim.x * kSpmmWarps;
+    C(*sv)[kMax] = s_val[warp];
+    int* sc = s_col[warp];
+    for (int grp = blockIdx.x * kSpmmWarps + warp; grp < n_groups; grp += nw) {
+        const int r0 = grp * G, r1 = min(r0 + G, n_rows);
+        const int b0 = __ldg(rp + r0), nb = __ldg(rp + r1) - b0;
+        if (nb > kMax) {  // not a voxel pattern (at most 27 blocks per row): read the blocks directly
+            const int row = r0 + g;
+            if (row < r1) {
+                C v[3];
+                row_product_colx<C, false>(val, stride, col, __ldg(rp + row), __ldg(rp + row + 1), x, 0, R, c, v[0],
+                                           v[1], v[2]);
+#pragma unroll
+                for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * R + c] = v[al];
+            }
+            continue;
+        }
+        for (int k = lane; k < nb; k += 32) {
+            sc[k] = __ldg(col + b0 + k);
+#pragma unroll
+            for (int q = 0; q < 9; ++q) sv[q][k] = __ldg(val + q * stride + b0 + k);
+        }
+        __syncwarp();
+        const int row = r0 + g;
+        if (row < r1) {
+            const int k0 = __ldg(rp + row) - b0, k1 = __ldg(rp + row + 1) - b0;
+            if constexpr (std::is_same<C, float4>::value) {
+                float a[3][4] = {};
+                for (int k = k0; k < k1; ++k) {
+                    const int xb = 3 * sc[k] * R + c;
+                    const float4 x0 = __ldg(x + xb), x1 = __ldg(x + xb + R), x2 = __ldg(x + xb + 2 * R);
+#pragma unroll
+                    for (int al = 0; al < 3; ++al) {
+                        dfc_mac(a[al], sv[3 * al][k], x0);
+                        dfc_mac(a[al], sv[3 * al + 1][k], x1);
+                        dfc_mac(a[al], sv[3 * al + 2][k], x2);
+                    }
+                }
+#pragma unroll
+                for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * R + c] = df_result_norm(a[al]);
+            } else {
+                using Tr = decltype(C{}.x);
+                Tr a[6] = {0, 0, 0, 0, 0, 0};
+                for (int k = k0; k < k1; ++k) {
+                    const int xb = 3 * sc[k] * R + c;
+                    const C xv[3] = {__ldg(x + xb), __ldg(x + xb + R), __ldg(x + xb + 2 * R)};
+#pragma unroll
+                    for (int al = 0; al < 3; ++al)
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) {
+                            const C m = sv[3 * al + be][k];
+                            a[2 * al] += m.x * xv[be].x - m.y * xv[be].y;
+                            a[2 * al + 1] += m.x * xv[be].y + m.y * xv[be].x;
+                        }
+                }
+#pragma unroll
+                for (int al = 0; al < 3; ++al) y[(size_t)(3 * row + al) * R + c] = mk(a[2 * al], a[2 * al + 1]);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <typename C>
+static void launch_spmm_rows(int R, cudaStream_t st, int sms, const C* val, int64_t stride, const int* col,
+                             const int* rp, const C* x, C* y, int n_rows) {
+    const int G = 32 / R;
+    const int64_t groups = ((int64_t)n_rows + G - 1) / G;
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * 16,
+                                                                            (groups + kSpmmWarps - 1) / kSpmmWarps));
+    switch (R) {
+        case 8: k_spmm_rows<C, 8><<<blocks, 32 * kSpmmWarps, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        case 16: k_spmm_rows<C, 16><<<blocks, 32 * kSpmmWarps, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+        default: k_spmm_rows<C, 32><<<blocks, 32 * kSpmmWarps, 0, st>>>(val, stride, col, rp, x, y, n_rows); break;
+    }
+}
+
 template <typename C>
 static void launch_spmv_warp(int R, unsigned blocks, cudaStream_t st, const C* val, int64_t stride, const int* col,
                              const int* rp, const C* x, C* y, int n_rows) {
@@ -135,7 +235,10 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
     const int64_t n_items = (int64_t)m->n_act * nrhs;
     const unsigned col_blocks = (unsigned)((n_items + 255) / 256);
     if (precision == FE_PREC_FP64) {
-        if (pow2)
+        if (pow2 && nrhs >= 8)
+            launch_spmm_rows<double2>(nrhs, st, ctx->num_sms, (const double2*)s->val64.ptr, s->stride, col, rp,
+                                  (const double2*)x, (double2*)y, m->n_act);
+        else if (pow2)
             launch_spmv_warp<double2>(nrhs, warp_blocks, st, (const double2*)s->val64.ptr, s->stride, col, rp,
                                   (const double2*)x, (double2*)y, m->n_act);
         else
@@ -146,7 +249,10 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
             set_error("fe_spmv: no complex64 copy (system assembled in FP64)");
             return FE_ERR_INVALID_ARG;
         }
-        if (pow2)
+        if (pow2 && nrhs >= 8)
+            launch_spmm_rows<float2>(nrhs, st, ctx->num_sms, (const float2*)s->val32.ptr, s->stride, col, rp,
+                                  (const float2*)x, (float2*)y, m->n_act);
+        else if (pow2)
             launch_spmv_warp<float2>(nrhs, warp_blocks, st, (const float2*)s->val32.ptr, s->stride, col, rp,
                                   (const float2*)x, (float2*)y, m->n_act);
         else
@@ -157,7 +263,10 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
             set_error("fe_spmv: no FP32-pair copy (system not assembled with FE_PREC_DF)");
             return FE_ERR_INVALID_ARG;
         }
-        if (pow2)
+        if (pow2 && nrhs >= 8)
+            launch_spmm_rows<float4>(nrhs, st, ctx->num_sms, (const float4*)s->valdf.ptr, s->stride, col, rp,
+                                  (const float4*)x, (float4*)y, m->n_act);
+        else if (pow2)
             launch_spmv_warp<float4>(nrhs, warp_blocks, st, (const float4*)s->valdf.ptr, s->stride, col, rp,
                                   (const float4*)x, (float4*)y, m->n_act);
         else

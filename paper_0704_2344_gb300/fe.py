@@ -77,7 +77,8 @@ class fe_solve_opts(C.Structure):
 
 class fe_solve_stats(C.Structure):
     _fields_ = [("kernel_ms", C.c_double), ("launches", C.c_int64), ("inner_iters", C.c_int64),
-                ("passes", C.c_int64), ("tile_width", C.c_int64), ("grid_ctas", C.c_int64)]
+                ("passes", C.c_int64), ("tile_width", C.c_int64), ("grid_ctas", C.c_int64),
+                ("tuned", C.c_int64), ("tune_ms", C.c_double)]
 
 
 class fe_solve_report(C.Structure):
@@ -192,7 +193,8 @@ def fe_launch_count() -> int:
 def fe_last_solve_stats(ctx) -> dict:
     s = fe_solve_stats()
     _check(load().fe_last_solve_stats(ctx, C.byref(s)), "fe_last_solve_stats")
-    return {n: (float(getattr(s, n)) if n == "kernel_ms" else int(getattr(s, n))) for n, _ in fe_solve_stats._fields_}
+    return {n: (float(getattr(s, n)) if n in ("kernel_ms", "tune_ms") else int(getattr(s, n)))
+            for n, _ in fe_solve_stats._fields_}
 
 
 def _ptr(a) -> int:

@@ -203,3 +203,59 @@ def test_mesh_rules():
     p.material[0, 0, 0] = 1
     with pytest.raises(ValueError):
         fem.assemble(p)
+
+
+def _centred_quarter(c, margin, kind):
+    """A cube of c elements (eps_r = 4 dielectric or PEC) centred in a box of
+    c + 2 margin elements at lambda/10, the box centred on the origin, reduced
+    to its +x, +y quarter by the mirror planes of normal incidence (H along x:
+    x = 0 is an antisymmetry plane, y = 0 a symmetry plane)."""
+    n = c + 2 * margin
+    prob = W.empty_box(n, 3e9, 10.0, name=f"{kind}{c}_m{margin}")
+    h = prob.h[0]
+    prob.origin = (-n / 2 * h, -n / 2 * h, -n / 2 * h)
+    if kind == "pec":
+        prob.material[margin:margin + c, margin:margin + c, margin:margin + c] = W.PEC
+    else:
+        prob.material[margin:margin + c, margin:margin + c, margin:margin + c] = 1
+        prob.eps_r = np.array([1.0 + 0j, 4.0 + 0j])
+        prob.mu_r = np.array([1.0 + 0j, 1.0 + 0j])
+    return W.mirror_part(prob, x_kind=2, y_kind=1)
+
+
+def _box_size_difference(c, m_small, m_big, sigma, kind, rim):
+    """Relative difference of the fields of two box sizes on the small box's
+    nodes at least `rim` elements inside its absorbing faces (Eq. 3 with
+    transverse-term sign sigma)."""
+    waves = W.normal_incidence()
+    out = []
+    for m in (m_small, m_big):
+        prob = _centred_quarter(c, m, kind)
+        maps = fem.mesh_maps(prob)
+        A = fem.assemble(prob, maps=maps, sigma=sigma)
+        B = fem.rhs(prob, waves, maps=maps, sigma=sigma)
+        x = fem.solve_direct(A, B)[:, 0].reshape(-1, 3)
+        pos = np.round(fem.node_positions(prob, maps) / prob.h[0]).astype(np.int64)
+        out.append((pos, x))
+    (ps, xs), (pb, xb) = out
+    index = {tuple(p): i for i, p in enumerate(pb)}
+    xb = xb[[index[tuple(p)] for p in ps]]
+    lim = (c + 2 * m_small) / 2 - rim
+    inner = np.all(np.abs(ps) <= lim, axis=1)
+    return np.linalg.norm(xs[inner] - xb[inner]) / np.linalg.norm(xb[inner])
+
+
+@pytest.mark.slow
+def test_box_size_accuracy_orders_the_abc_terms():
+    """The box-size accuracy study of the absorbing condition (Eq. 3), on the
+    oracle: an eps_r = 4 cube of 0.4 wavelength, boxes with 0.4 and 1.2
+    wavelengths of margin.  Close to the scatterer the field at the outer
+    faces has strong evanescent content: the first-order condition (sigma = 0)
+    differs least from the larger box, the transverse term as printed (sigma
+    = +1, which damps evanescent modes a little more) a little more, and the
+    opposite sign (sigma = -1, whose boundary amplifies evanescent modes with
+    tangential wavenumbers above sqrt(2) k0) most.  A sign error in the
+    oracle's transverse term would swap the last two."""
+    d = {s: _box_size_difference(4, 4, 12, s, "diel", 3) for s in (-1.0, 0.0, 1.0)}
+    assert d[0.0] < d[1.0] < d[-1.0]
+    assert d[-1.0] < 0.3 and d[1.0] < 1.2 * d[0.0]
