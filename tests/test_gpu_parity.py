@@ -213,16 +213,19 @@ def _spmv_check(fe, ctx, prob, nrhs, seed=0):
     assert np.all(np.abs(y32h - ref) <= 4e-6 * bound)
 
 
-@pytest.mark.parametrize("nrhs", [1, 3, 8])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 16, 32])
 def test_spmv_small(fe, ctx, nrhs):
     _spmv_check(fe, ctx, W.random_small_grid(5, n_max=8, n_pec_boxes=2), nrhs)
 
 
-def test_spmv_config2(fe, ctx):
-    _spmv_check(fe, ctx, W.config2()[0], 1, seed=3)
+@pytest.mark.parametrize("nrhs", [1, 16])
+def test_spmv_config2(fe, ctx, nrhs):
+    """Full size: 29 666 block rows, so the products' row groups run over many
+    tiles and end in a ragged one."""
+    _spmv_check(fe, ctx, W.config2()[0], nrhs, seed=3)
 
 
-@pytest.mark.parametrize("nrhs", [1, 3])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 16])
 def test_spmv_fp32_pairs(fe, ctx, nrhs):
     """FE_PREC_DF product: FP32-pair matrix and vector, error-free product
     and sum steps.  Its error is a few 2^-48 of sum |a_ij x_j| per entry; the
