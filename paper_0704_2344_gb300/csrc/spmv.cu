@@ -3,6 +3,7 @@
 #include "krylov.cuh"
 
 #include <algorithm>
+#include <cstdint>
 #include <type_traits>
 
 namespace fe {
@@ -187,6 +188,140 @@ __global__ void __launch_bounds__(32 * kSpmmWarps) k_spmm_rows(const C* __restri
     }
 }
 
+// y = A x for R = 8, 16 or 32 complex64 columns, with several columns per
+// lane: CPL adjacent columns per lane, L = R / CPL lanes per row and G = 32 /
+// L rows per warp.  As in k_spmm_rows the warp first stages its rows' blocks
+// (nine planes and the column indices) in shared memory with coalesced
+// loads; each entry read from shared memory then serves CPL columns, and a
+// lane reads its CPL vector values of a block row with 16-byte loads.  PF
+// loads the next block's vector values one step ahead.
+template <int CPL>
+struct SpmmX;
+template <>
+struct SpmmX<2> {
+    float4 v[1];
+};
+template <>
+struct SpmmX<4> {
+    float4 v[2];
+};
+
+template <int R, int CPL>
+__device__ __forceinline__ void spmm_load_x(const float2* __restrict__ x, int cb, int c0, SpmmX<CPL> (&d)[3]) {
+#pragma unroll
+    for (int be = 0; be < 3; ++be) {
+        const float4* p = (const float4*)(x + (size_t)(3 * cb + be) * R + c0);
+#pragma unroll
+        for (int v = 0; v < CPL / 2; ++v) d[be].v[v] = __ldg(p + v);
+    }
+}
+
+template <int R, int CPL, int W, bool PF>
+__global__ void __launch_bounds__(32 * W) k_spmm_cpl(const float2* __restrict__ val, int64_t stride,
+                                                     const int* __restrict__ col, const int* __restrict__ rp,
+                                                     const float2* __restrict__ x, float2* __restrict__ y,
+                                                     int n_rows) {
+    constexpr int L = R / CPL, G = 32 / L, kMax = 27 * G;
+    __shared__ float2 s_val[W][9][kMax];
+    __shared__ int s_col[W][kMax];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int c0 = (lane % L) * CPL, g = lane / L;
+    const int n_groups = (n_rows + G - 1) / G;
+    float2(*sv)[kMax] = s_val[warp];
+    int* sc = s_col[warp];
+    for (int grp = blockIdx.x * W + warp; grp < n_groups; grp += gridDim.x * W) {
+        const int r0 = grp * G, r1 = min(r0 + G, n_rows);
+        const int b0 = __ldg(rp + r0), nb = __ldg(rp + r1) - b0;
+        const int row = r0 + g;
+        float a[3][CPL][2] = {};
+        if (nb > kMax) {  // not a voxel pattern (at most 27 blocks per row): read the blocks directly
+            if (row < r1)
+#pragma unroll
+                for (int j = 0; j < CPL; ++j) {
+                    float2 v[3];
+                    row_product_colx<float2, false>(val, stride, col, __ldg(rp + row), __ldg(rp + row + 1), x, 0, R,
+                                                    c0 + j, v[0], v[1], v[2]);
+#pragma unroll
+                    for (int al = 0; al < 3; ++al) {
+                        a[al][j][0] = v[al].x;
+                        a[al][j][1] = v[al].y;
+                    }
+                }
+        } else {
+            for (int k = lane; k < nb; k += 32) {
+                sc[k] = __ldg(col + b0 + k);
+#pragma unroll
+                for (int q = 0; q < 9; ++q) sv[q][k] = __ldg(val + q * stride + b0 + k);
+            }
+            __syncwarp();
+            if (row < r1) {
+                const int k0 = __ldg(rp + row) - b0, k1 = __ldg(rp + row + 1) - b0;
+                SpmmX<CPL> xn[3];
+                if (PF && k0 < k1) spmm_load_x<R, CPL>(x, sc[k0], c0, xn);
+                for (int k = k0; k < k1; ++k) {
+                    SpmmX<CPL> xv[3];
+                    if (PF) {
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) xv[be] = xn[be];
+                        if (k + 1 < k1) spmm_load_x<R, CPL>(x, sc[k + 1], c0, xn);
+                    } else {
+                        spmm_load_x<R, CPL>(x, sc[k], c0, xv);
+                    }
+#pragma unroll
+                    for (int al = 0; al < 3; ++al)
+#pragma unroll
+                        for (int be = 0; be < 3; ++be) {
+                            const float2 m = sv[3 * al + be][k];
+#pragma unroll
+                            for (int v = 0; v < CPL / 2; ++v) {
+                                const float4 q = xv[be].v[v];
+                                a[al][2 * v][0] += m.x * q.x - m.y * q.y;
+                                a[al][2 * v][1] += m.x * q.y + m.y * q.x;
+                                a[al][2 * v + 1][0] += m.x * q.z - m.y * q.w;
+                                a[al][2 * v + 1][1] += m.x * q.w + m.y * q.z;
+                            }
+                        }
+                }
+            }
+            __syncwarp();
+        }
+        if (row < r1)
+#pragma unroll
+            for (int al = 0; al < 3; ++al) {
+                float4* p = (float4*)(y + (size_t)(3 * row + al) * R + c0);
+#pragma unroll
+                for (int v = 0; v < CPL / 2; ++v)
+                    p[v] = make_float4(a[al][2 * v][0], a[al][2 * v][1], a[al][2 * v + 1][0], a[al][2 * v + 1][1]);
+            }
+    }
+}
+
+// Columns per lane, warps per CTA and prefetch for each width, chosen by
+// timing every combination on a 27-point pattern of 81^3 nodes (14.0 M
+// blocks) on GB300: R = 8 2 / 2 / on, R = 16 4 / 2 / off, R = 32 2 / 8 / off.
+template <int R, int CPL, int W, bool PF>
+static void launch_spmm_cpl_t(cudaStream_t st, int sms, const float2* val, int64_t stride, const int* col,
+                              const int* rp, const float2* x, float2* y, int n_rows) {
+    constexpr int G = 32 / (R / CPL);
+    int per_sm = 0;  // resident CTAs per SM (a host query, no device work)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_spmm_cpl<R, CPL, W, PF>, 32 * W, 0) != cudaSuccess ||
+        per_sm < 1)
+        per_sm = 1;
+    const int64_t groups = ((int64_t)n_rows + G - 1) / G;
+    const unsigned blocks =
+        (unsigned)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * per_sm, (groups + W - 1) / W));
+    k_spmm_cpl<R, CPL, W, PF><<<blocks, 32 * W, 0, st>>>(val, stride, col, rp, x, y, n_rows);
+}
+
+static void launch_spmm_cpl(int R, cudaStream_t st, int sms, const float2* val, int64_t stride, const int* col,
+                            const int* rp, const float2* x, float2* y, int n_rows) {
+    switch (R) {
+        case 8: launch_spmm_cpl_t<8, 2, 2, true>(st, sms, val, stride, col, rp, x, y, n_rows); break;
+        case 16: launch_spmm_cpl_t<16, 4, 2, false>(st, sms, val, stride, col, rp, x, y, n_rows); break;
+        default: launch_spmm_cpl_t<32, 2, 8, false>(st, sms, val, stride, col, rp, x, y, n_rows); break;
+    }
+}
+
 template <typename C>
 static void launch_spmm_rows(int R, cudaStream_t st, int sms, const C* val, int64_t stride, const int* col,
                              const int* rp, const C* x, C* y, int n_rows) {
@@ -249,7 +384,11 @@ fe_status fe_spmv(fe_ctx* ctx, const fe_system* s, int32_t precision, int32_t nr
             set_error("fe_spmv: no complex64 copy (system assembled in FP64)");
             return FE_ERR_INVALID_ARG;
         }
-        if (pow2 && nrhs >= 8)
+        const bool aligned16 = (((uintptr_t)x | (uintptr_t)y) & 15) == 0;  // the lanes' 16-byte vector accesses
+        if (pow2 && nrhs >= 8 && aligned16)
+            launch_spmm_cpl(nrhs, st, ctx->num_sms, (const float2*)s->val32.ptr, s->stride, col, rp,
+                            (const float2*)x, (float2*)y, m->n_act);
+        else if (pow2 && nrhs >= 8)
             launch_spmm_rows<float2>(nrhs, st, ctx->num_sms, (const float2*)s->val32.ptr, s->stride, col, rp,
                                   (const float2*)x, (float2*)y, m->n_act);
         else if (pow2)
