@@ -61,6 +61,8 @@ def parse():
     ap.add_argument("--seq-sample", type=int, default=24,
                     help="config5: requests (a seeded random sample) timed through the sequential FP64 path")
     ap.add_argument("--serve-precision", default="df", choices=["df", "fp64", "mixed"])
+    ap.add_argument("--no-poisson", action="store_true",
+                    help="config5: skip the Poisson-arrival pass (latency then from the t = 0 pass)")
     ap.add_argument("--serve-only", action="store_true",
                     help="config5: only the all-at-t=0 serving pass (no sequential baseline, no Poisson pass)")
     ap.add_argument("--max-job-ctas", type=int, default=0, help="config5: CTAs one request may take (0: default)")
@@ -662,7 +664,7 @@ def run_serving(args, rank, world, local_rank):
     print(f"config5: sequential FP64 sample of {len(seq_times)} requests in {seq_wall:.1f} s ({seq_ok} converged)",
           file=sys.stderr, flush=True)
 
-    if args.serve_only:
+    if args.serve_only or args.no_poisson:
         lat_wall, lat_res, lat_info = float("nan"), res, info
         mean_gap = None
     else:
@@ -705,7 +707,7 @@ def run_serving(args, rank, world, local_rank):
                             "p99_s": round(float(np.percentile(seq_times, 99)), 5) if seq_times else None,
                             "sample": "seeded random requests of the stream, each alone in FP64"},
         "speedup_vs_sequential_fp64": round(value / seq_rate, 3) if seq_times else None,
-        "latency": {"arrival": "all at t=0 (--serve-only)" if args.serve_only else
+        "latency": {"arrival": "all at t=0" if (args.serve_only or args.no_poisson) else
                     "poisson at 80 % of the measured serving capacity",
                     "mean_gap_s": round(mean_gap, 5) if mean_gap else None,
                     "p50_s": round(float(np.percentile(lat, 50)), 5), "p99_s": round(float(np.percentile(lat, 99)), 5),
