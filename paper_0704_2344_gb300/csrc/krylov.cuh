@@ -87,6 +87,88 @@ __device__ __forceinline__ void df_norm(float& h, float& l) {
     h = t;
 }
 
+// ---- FP32-pair scalar arithmetic, for the per-column recurrence scalars of
+// the FP32-pair solve.  On GB300 one dependent FP64 operation of a thread
+// takes about 64 cycles and one FP32 operation about 5, so a chain of a few
+// dozen FP64 operations that every CTA repeats after each grid reduction costs
+// more than its FP32-pair equivalent.  A real pair is a float2 (h, l) with
+// value h + l; a complex pair is a float4 (re_h, im_h, re_l, im_l) as in the
+// vectors, or a DZ of two real pairs.
+__device__ __forceinline__ float2 dd_fast_two_sum(float a, float b) {  // needs |a| >= |b| or a = 0 (Dekker)
+    const float s = __fadd_rn(a, b);
+    return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ float2 dd_two_sum(float a, float b) {  // Knuth's TwoSum
+    const float s = __fadd_rn(a, b);
+    const float v = __fsub_rn(s, a);
+    return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, v)), __fsub_rn(b, v)));
+}
+
+// a + b, accurate under cancellation too: the two high parts and the two low
+// parts by TwoSum, then two renormalisations (the accurate pair addition of
+// Joldes, Muller and Popescu, ACM TOMS 2017, Algorithm 6)
+__device__ __forceinline__ float2 dd_add(float2 a, float2 b) {
+    const float2 s = dd_two_sum(a.x, b.x);
+    const float2 t = dd_two_sum(a.y, b.y);
+    const float2 u = dd_fast_two_sum(s.x, __fadd_rn(s.y, t.x));
+    return dd_fast_two_sum(u.x, __fadd_rn(u.y, t.y));
+}
+
+__device__ __forceinline__ float2 dd_neg(float2 a) { return make_float2(-a.x, -a.y); }
+
+// a b: the exact error of a.h b.h from one FMA, the cross terms added to it
+// (a.l b.l, about 2^-48 relative, dropped)
+__device__ __forceinline__ float2 dd_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = __fmaf_rn(a.x, b.x, -p);
+    e = __fmaf_rn(a.x, b.y, e);
+    e = __fmaf_rn(a.y, b.x, e);
+    return dd_fast_two_sum(p, e);
+}
+
+// a / b: a first FP32 quotient, the remainder a - q1 b in pair arithmetic,
+// and its quotient as the correction (Dekker, Numer. Math. 1971)
+__device__ __forceinline__ float2 dd_div(float2 a, float2 b) {
+    const float q1 = __fdiv_rn(a.x, b.x);
+    const float2 r = dd_add(a, dd_neg(dd_mul(make_float2(q1, 0.f), b)));
+    return dd_fast_two_sum(q1, __fdiv_rn(r.x, b.x));
+}
+
+struct DZ {
+    float2 re, im;
+};
+
+__device__ __forceinline__ DZ dz_of(const float4& v) { return {make_float2(v.x, v.z), make_float2(v.y, v.w)}; }
+__device__ __forceinline__ float4 dz_f4(const DZ& a) { return make_float4(a.re.x, a.im.x, a.re.y, a.im.y); }
+__device__ __forceinline__ DZ dz_add(const DZ& a, const DZ& b) { return {dd_add(a.re, b.re), dd_add(a.im, b.im)}; }
+__device__ __forceinline__ DZ dz_sub(const DZ& a, const DZ& b) {
+    return {dd_add(a.re, dd_neg(b.re)), dd_add(a.im, dd_neg(b.im))};
+}
+__device__ __forceinline__ DZ dz_mul(const DZ& a, const DZ& b) {
+    return {dd_add(dd_mul(a.re, b.re), dd_neg(dd_mul(a.im, b.im))), dd_add(dd_mul(a.re, b.im), dd_mul(a.im, b.re))};
+}
+
+// a / b by Smith's method (Comm. ACM 1962): no square of b is formed, so the
+// FP32 exponent range holds whenever a, b and the quotient do.
+__device__ __forceinline__ DZ dz_div(const DZ& a, const DZ& b) {
+    const float2 one = make_float2(1.f, 0.f);
+    if (fabsf(b.re.x) >= fabsf(b.im.x)) {
+        const float2 t = dd_div(b.im, b.re);
+        const float2 inv = dd_div(one, dd_add(b.re, dd_mul(b.im, t)));
+        return {dd_mul(dd_add(a.re, dd_mul(a.im, t)), inv), dd_mul(dd_add(a.im, dd_neg(dd_mul(a.re, t))), inv)};
+    }
+    const float2 t = dd_div(b.re, b.im);
+    const float2 inv = dd_div(one, dd_add(dd_mul(b.re, t), b.im));
+    return {dd_mul(dd_add(dd_mul(a.re, t), a.im), inv), dd_mul(dd_add(dd_mul(a.im, t), dd_neg(a.re)), inv)};
+}
+
+// a finite, nonzero complex pair (its high parts decide)
+__device__ __forceinline__ bool dz_usable(const DZ& a) {
+    const float m = fabsf(a.re.x) + fabsf(a.im.x);
+    return m > 0.f && m <= 3.0e38f;
+}
+
 // Accumulator -> stored complex FP32 pair, renormalised.
 __device__ __forceinline__ float4 df_result_norm(float (&acc)[4]) {
     df_norm(acc[0], acc[1]);

@@ -43,6 +43,7 @@ inline size_t sync_bytes(int n_cta) {
 struct ColState {
     double bn, rr_ref, rel, gam_r, gam_i, al_r, al_i, be_r, be_i, igam_r, igam_i, ial_r, ial_i, pad;
     float4 a4, na4, b4;
+    float4 gam4, igam4, ial4;  // FP32-pair solves: gamma, 1/gamma, 1/alpha as pairs
     int active, done, status, iters, outer, first, refresh, repl, pass_it, pad2[3];
 };
 struct JobState {
@@ -178,10 +179,10 @@ __device__ __forceinline__ void grid_barrier_init() {
     if (threadIdx.x == 0) g_bar_epoch = 0u;
 }
 
-// kPair: the partials travel and are summed as FP32 pairs (hi = RN32(v),
-// lo = RN32(v - hi); TwoSum additions), on the FP32 pipes.  On this GPU a
-// warp's FP64 instruction holds the SM's FP64 pipe for about 16 cycles, so
-// sums that every CTA repeats are kept off it.
+// kPair: s_in and s_out hold FP32 pairs (a float2 (h, l) in each 8-byte
+// slot), and the partials travel and are summed as pairs (TwoSum additions)
+// on the FP32 pipes.  On this GPU one FP64 instruction of a warp takes about
+// 64 cycles, so sums that every CTA repeats are kept off the FP64 pipe.
 template <int NV, bool kPair = false>
 __device__ __noinline__ bool grid_reduce(const SolveParams& P, int cta, const double* s_in, double* s_out) {
     __shared__ int s_ok;
@@ -190,8 +191,7 @@ __device__ __noinline__ bool grid_reduce(const SolveParams& P, int cta, const do
     double* part = P.partial + (size_t)(ep & 1u) * (size_t)P.part_half;
     for (int v = threadIdx.x; v < NV; v += kThreads) {
         if (kPair) {
-            const float hi = __double2float_rn(s_in[v]);
-            ((float2*)part)[(size_t)cta * NV + v] = make_float2(hi, __double2float_rn(s_in[v] - (double)hi));
+            ((float2*)part)[(size_t)cta * NV + v] = ((const float2*)s_in)[v];
         } else {
             part[(size_t)cta * NV + v] = s_in[v];
         }
@@ -234,7 +234,10 @@ __device__ __noinline__ bool grid_reduce(const SolveParams& P, int cta, const do
                     const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
                     df_add(h, l, h2, l2);
                 }
-                if (lane == 0) s_out[v] = (double)h + (double)l;
+                if (lane == 0) {
+                    df_norm(h, l);
+                    ((float2*)s_out)[v] = make_float2(h, l);
+                }
             } else {
                 double acc = 0.0;
                 for (int c = lane; c < P.n_cta; c += 32) acc += __ldcg(part + (size_t)c * NV + v);
@@ -298,7 +301,10 @@ __device__ __forceinline__ void cta_colsum_df(const float (&f)[2 * NV], double* 
             const float h2 = __shfl_xor_sync(0xffffffffu, h, o), l2 = __shfl_xor_sync(0xffffffffu, l, o);
             df_add(h, l, h2, l2);
         }
-        if (lane == 0) s_in[i] = (double)h + (double)l;
+        if (lane == 0) {
+            df_norm(h, l);
+            ((float2*)s_in)[i] = make_float2(h, l);  // a pair, read as such by grid_reduce<NV, true>
+        }
     }
     __syncthreads();
 }
@@ -1115,6 +1121,23 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     __shared__ double s_gam_r[R], s_gam_i[R], s_al_r[R], s_al_i[R], s_be_r[R], s_be_i[R];
     __shared__ double s_igam_r[R], s_igam_i[R], s_ial_r[R], s_ial_i[R];  // 1/gamma, 1/alpha of the last iteration
     __shared__ float4 s_a4[R], s_na4[R], s_b4[R];  // alpha, -alpha, beta as FP32 pairs (FP32-pair updates)
+    // FP32-pair solves keep gamma, 1/gamma and 1/alpha of the last iteration as
+    // FP32 pairs, and 1/||b||^2 and 1/rr_ref in FP32 for the convergence tests
+    // (s_scl_ok: both are normal FP32 numbers)
+    __shared__ float4 s_gam4[kDFV ? R : 1], s_igam4[kDFV ? R : 1], s_ial4[kDFV ? R : 1];
+    __shared__ float s_ibn2f[kDFV ? R : 1], s_irrf[kDFV ? R : 1];
+    __shared__ int s_scl_ok[kDFV ? R : 1];
+    // FP32 forms of 1/||b||^2 and 1/rr_ref, set whenever those change (rare)
+    auto set_scales = [&](int c) {
+        if constexpr (kDFV) {
+            const double b2 = s_bn[c] * s_bn[c];
+            const double ib = b2 > 0.0 ? 1.0 / b2 : 0.0, ir = s_rr_ref[c] > 0.0 ? 1.0 / s_rr_ref[c] : 0.0;
+            s_ibn2f[c] = (float)ib;
+            s_irrf[c] = (float)ir;
+            s_scl_ok[c] = ib > 1.0e-37 && ib < 1.0e37 && ir > 1.0e-37 && ir < 1.0e37;
+        }
+    };
+    const float tol2f = (float)(P.tol * P.tol), rel2f = (float)(P.reliable * P.reliable);
     __shared__ int s_bmask[R];  // columns a block incomplete Cholesky application writes
     __shared__ int s_active[R], s_done[R], s_status[R], s_iters[R], s_outer[R], s_first[R], s_refresh[R],
         s_repl[R], s_pass_it[R];
@@ -1230,6 +1253,12 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             s_a4[tid] = cs.a4;
             s_na4[tid] = cs.na4;
             s_b4[tid] = cs.b4;
+            if constexpr (kDFV) {
+                s_gam4[tid] = cs.gam4;
+                s_igam4[tid] = cs.igam4;
+                s_ial4[tid] = cs.ial4;
+                set_scales(tid);
+            }
             s_active[tid] = cs.active;
             s_done[tid] = cs.done;
             s_status[tid] = cs.status;
@@ -1360,6 +1389,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     } else {
                         s_active[c] = 1;
                         s_rr_ref[c] = rn * rn;
+                        set_scales(c);
                         s_pass_it[c] = 0;
                         s_refresh[c] = s_first[c] ? 0 : 1;
                     }
@@ -1429,7 +1459,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         // and 1/alpha = conj(alpha) / |alpha|^2 of the last iteration.
         if (tid >= kThreads - R) {
             const int c = kThreads - 1 - tid;
-            if (s_active[c] && !s_first[c]) {
+            if constexpr (kDFV) {  // the same in FP32-pair arithmetic
+                if (s_active[c] && !s_first[c]) {
+                    const DZ one = {make_float2(1.f, 0.f), make_float2(0.f, 0.f)};
+                    s_igam4[c] = dz_f4(dz_div(one, dz_of(s_gam4[c])));
+                    s_ial4[c] = dz_f4(dz_div(one, dz_of(s_a4[c])));
+                }
+            } else if (s_active[c] && !s_first[c]) {
                 const double ig = rcp64(s_gam_r[c] * s_gam_r[c] + s_gam_i[c] * s_gam_i[c]);
                 const double ia = rcp64(s_al_r[c] * s_al_r[c] + s_al_i[c] * s_al_i[c]);
                 s_igam_r[c] = s_gam_r[c] * ig;
@@ -1473,11 +1509,25 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         if (tid < R) {
             const int c = tid;
             if (s_active[c]) {
-                const double rr = s_out[4 * R + c];
-                const double tb = P.tol * s_bn[c];
-                const bool small = rr <= tb * tb || rr < P.reliable * P.reliable * s_rr_ref[c];
+                bool small, nan;
+                if constexpr (kDFV) {  // |r|^2 as an FP32 pair; the tests scaled into FP32 range
+                    const float2 q = ((const float2*)s_out)[4 * R + c];
+                    const float rr = __fadd_rn(q.x, q.y);
+                    nan = !(rr == rr);
+                    if (s_scl_ok[c]) {
+                        small = rr * s_ibn2f[c] <= tol2f || rr * s_irrf[c] < rel2f;
+                    } else {
+                        const double rd = (double)q.x + (double)q.y, tb = P.tol * s_bn[c];
+                        small = rd <= tb * tb || rd < P.reliable * P.reliable * s_rr_ref[c];
+                    }
+                } else {
+                    const double rr = s_out[4 * R + c];
+                    const double tb = P.tol * s_bn[c];
+                    small = rr <= tb * tb || rr < P.reliable * P.reliable * s_rr_ref[c];
+                    nan = !(rr == rr);
+                }
                 const bool stalled = P.restart && P.max_pass > 0 && s_pass_it[c] >= P.max_pass;
-                if (!(rr == rr) || s_iters[c] >= P.max_iter || (!s_first[c] && (small || stalled))) {
+                if (nan || s_iters[c] >= P.max_iter || (!s_first[c] && (small || stalled))) {
                     s_repl[c] = 1;
                     if (P.restart) s_first[c] = 1;
                 }
@@ -1507,7 +1557,48 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         // beta gamma (1/alpha_old) need no division: the one reciprocal on the
         // dependent chain is that of |e|^2.  FP64 operations of one thread
         // have a long latency on this GPU.
-        if (tid < R) {
+        if constexpr (kDFV) {  // the same recurrences in FP32-pair arithmetic
+            if (tid < R) {
+                const int c = tid;
+                if (s_active[c]) {
+                    const float2* so = (const float2*)s_out;
+                    const float2 zero = make_float2(0.f, 0.f);
+                    const DZ g = {so[c], so[R + c]}, d = {so[2 * R + c], so[3 * R + c]};
+                    DZ b = {zero, zero}, e = d;
+                    if (!s_first[c]) {
+                        b = dz_mul(g, dz_of(s_igam4[c]));  // beta = gamma / gamma_old
+                        if (s_refresh[c]) {
+                            // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
+                            const DZ e12 = {dd_add(so[5 * R + c], so[7 * R + c]), dd_add(so[6 * R + c], so[8 * R + c])};
+                            const DZ e3 = {so[9 * R + c], so[10 * R + c]};
+                            e = dz_add(dz_add(d, dz_mul(b, e12)), dz_mul(dz_mul(b, b), e3));
+                        } else {
+                            e = dz_sub(d, dz_mul(dz_mul(b, g), dz_of(s_ial4[c])));  // delta - beta gamma / alpha_old
+                        }
+                    }
+                    s_b4[c] = dz_f4(b);
+                    if (!dz_usable(e) || !dz_usable(g)) {
+                        if (s_first[c]) {  // breakdown right after a (re)start
+                            s_active[c] = 0;
+                            s_done[c] = 1;
+                            s_status[c] = FE_ERR_BREAKDOWN;
+                        } else {  // restart from the true residual next round
+                            s_repl[c] = 1;
+                            s_first[c] = 1;
+                        }
+                    } else {
+                        const float4 a4 = dz_f4(dz_div(g, e));
+                        s_a4[c] = a4;
+                        s_na4[c] = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
+                        s_gam4[c] = dz_f4(g);
+                        s_iters[c] += 1;
+                        s_pass_it[c] += 1;
+                        s_first[c] = 0;
+                        s_refresh[c] = 0;
+                    }
+                }
+            }
+        } else if (tid < R) {
             const int c = tid;
             if (s_active[c]) {
                 const double gr = s_out[c], gi = s_out[R + c];
@@ -1687,6 +1778,11 @@ out:
                 cs.a4 = s_a4[tid];
                 cs.na4 = s_na4[tid];
                 cs.b4 = s_b4[tid];
+                if constexpr (kDFV) {
+                    cs.gam4 = s_gam4[tid];
+                    cs.igam4 = s_igam4[tid];
+                    cs.ial4 = s_ial4[tid];
+                }
                 cs.active = s_active[tid];
                 cs.done = s_done[tid];
                 cs.status = s_status[tid];
