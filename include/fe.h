@@ -81,9 +81,12 @@ typedef enum fe_variant {
 typedef enum fe_precision {
     FE_PREC_FP64 = 0,  /* plain method: complex128 matrix, complex128 Krylov loop */
     FE_PREC_MIXED = 1, /* complex64 Krylov loop inside FP64 iterative refinement */
-    FE_PREC_DF = 2     /* Krylov products on FP32 pairs ("double-float", about 48 significant bits:
-                          hi = RN32(v), lo = RN32(v - hi), products by error-free transformations on
-                          the FP32 pipes), everything else FP64; converges like FE_PREC_FP64 */
+    FE_PREC_DF = 2     /* the Krylov loop on FP32 pairs ("double-float", about 48 significant bits:
+                          hi = RN32(v), lo = RN32(v - hi), products and sums by error-free
+                          transformations on the FP32 pipes): products, vectors, inner products and
+                          the recurrence scalars; the true residual, the refinement and the solution
+                          FP64.  Converges like FE_PREC_FP64 on well-behaved systems (a few percent
+                          more iterations) */
 } fe_precision;
 
 /* The field solved for (Section 2: every step of the H formulation applies
@@ -297,10 +300,10 @@ fe_status fe_spmv_half(fe_ctx* ctx, const fe_system* s, int32_t precision, int32
  * and the preconditioner stay FP64; each time the recursive residual has
  * dropped by `reliable`, the FP64 true residual b - A x replaces it and the
  * directions restart (FP64 iterative refinement around complex64 Krylov
- * passes).  FE_PREC_DF runs those products on the FP32-pair copy (about
- * 48 significant bits on the FP32 pipes, which GB300 issues at 64 times the
- * FP64 rate) and, like FE_PREC_FP64, keeps the directions across true-residual
- * refreshes.  The true residual decides convergence: ||b - A x|| / ||b|| <= tol
+ * passes).  FE_PREC_DF runs the whole Krylov loop in FP32 pairs (about 48
+ * significant bits on the FP32 pipes, which GB300 issues at 64 times the FP64
+ * rate): products, vectors, inner products and the recurrence scalars; like
+ * FE_PREC_FP64 it keeps the directions across true-residual refreshes.  The true residual decides convergence: ||b - A x|| / ||b|| <= tol
  * for every right-hand side.  Up to
  * rhs_tile right-hand sides are solved together in one persistent device
  * launch.  With rhs_tile = 0 and at least 8 right-hand sides, the first solve
