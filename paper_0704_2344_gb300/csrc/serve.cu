@@ -384,6 +384,7 @@ void fe_serve_opts_default(fe_serve_opts* o) {
     o->work_per_cta = 2048;
     o->max_job_ctas = 0;
     o->seg_iters = 0;
+    o->recurrence = FE_RECURRENCE_CG;
 }
 
 int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,
@@ -419,7 +420,8 @@ fe_status fe_serve_create(fe_ctx* ctx, const fe_serve_opts* opt, fe_server** out
     if ((o.precision != FE_PREC_FP64 && o.precision != FE_PREC_MIXED && o.precision != FE_PREC_DF) ||
         !(o.tol > 0.0) || o.max_iter < 1 ||
         o.max_outer < 1 || !(o.reliable >= 0.0 && o.reliable < 1.0) || o.hbm_budget < 0 || o.max_ctas < 0 ||
-        o.max_job_ctas < 0 || o.seg_iters < 0) {
+        o.max_job_ctas < 0 || o.seg_iters < 0 ||
+        (o.recurrence != FE_RECURRENCE_CG && o.recurrence != FE_RECURRENCE_EXPANDED)) {
         set_error("fe_serve_create: option out of range");
         return FE_ERR_INVALID_ARG;
     }
@@ -436,6 +438,7 @@ fe_status fe_serve_create(fe_ctx* ctx, const fe_serve_opts* opt, fe_server** out
     S->so.reliable = o.reliable;
     S->so.max_iter = o.max_iter;
     S->so.max_outer = o.max_outer;
+    S->so.recurrence = o.recurrence;
     fe_options io = ctx->opt;
     io.stream = nullptr;  // the server's own stream
     fe_status e = fe_ctx_create(&S->ictx, ctx->device, &io);

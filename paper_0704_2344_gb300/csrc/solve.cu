@@ -234,6 +234,7 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
     P.timeout_ns = 1000ull * (unsigned long long)(o.wait_timeout_us > 0 ? o.wait_timeout_us : 4000000);
     P.spin_ns = 0;  // barrier waits poll without back-off (measured fastest)
+    P.expand = o.recurrence == FE_RECURRENCE_EXPANDED ? 1 : 0;
     if (o.preconditioner == FE_PRECOND_BICP && fp64) {
         P.bicp_l = (const double2*)s->bicp_l.ptr;
         P.bicp_linv = (const double2*)s->bicp_linv.ptr;
@@ -663,6 +664,10 @@ static fe_status check_opts(const fe_solve_opts* o, fe_solve_opts& out) {
         set_error("solve: bad tolerance or iteration limits");
         return FE_ERR_INVALID_ARG;
     }
+    if (out.recurrence != FE_RECURRENCE_CG && out.recurrence != FE_RECURRENCE_EXPANDED) {
+        set_error("solve: unknown recurrence %d", (int)out.recurrence);
+        return FE_ERR_INVALID_ARG;
+    }
     if (out.preconditioner != FE_PRECOND_BLOCK_JACOBI && out.preconditioner != FE_PRECOND_BICP) {
         set_error("solve: unknown preconditioner %d", (int)out.preconditioner);
         return FE_ERR_INVALID_ARG;
@@ -707,6 +712,7 @@ void fe_solve_opts_default(fe_solve_opts* o) {
     o->max_pass_iter = 2000;
     o->wait_timeout_us = 4000000;
     o->preconditioner = FE_PRECOND_BLOCK_JACOBI;
+    o->recurrence = FE_RECURRENCE_CG;
 }
 
 fe_status fe_solve_rhs(fe_ctx* ctx, const fe_system* s, int32_t nrhs, const void* b, int32_t b_on_device,

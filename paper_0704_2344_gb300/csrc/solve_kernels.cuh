@@ -135,6 +135,8 @@ struct SolveParams {
     unsigned long long* trace;  // optional [n_cta][kTraceIters][kTracePhases] timestamps
     unsigned long long timeout_ns;
     unsigned spin_ns;           // back-off between polls of the barrier generation
+    int expand;                 // p^T A p of every iteration from its three dots (u^T s, p^T w, p^T s) with the
+                                // recursive s, not from the Chronopoulos-Gear recurrence
     // block incomplete Cholesky factor, one band per CTA (FP64 solves; null:
     // block Jacobi)
     const double2* bicp_l;      // [nnzb * 9] L_IJ by block slot, row-major 3x3
@@ -684,6 +686,11 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             dfc_mac4(facc + 14 % (2 * NV), pv, wy);
             dfc_mac4(facc + 18 % (2 * NV), pv, sy);
             ((float4*)P.s)[o] = sy;
+          } else if (P.expand) {  // the same dots with the recursive s
+            const float4 pv = ld_cg((const float4*)P.p + o), sv = ld_cg((const float4*)P.s + o);
+            dfc_mac4(facc + 10 % (2 * NV), uv, sv);
+            dfc_mac4(facc + 14 % (2 * NV), pv, wy);
+            dfc_mac4(facc + 18 % (2 * NV), pv, sv);
           }
         }
       } else {
@@ -703,6 +710,14 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             acc[9 % NV] += pv.x * sd.x - pv.y * sd.y;
             acc[10 % NV] += pv.x * sd.y + pv.y * sd.x;
             P.s[o] = sd;
+          } else if (P.expand) {  // the same dots with the recursive s
+            const double2 pv = __ldcg(P.p + o), sd = __ldcg(P.s + o);
+            acc[5 % NV] += uv.x * sd.x - uv.y * sd.y;
+            acc[6 % NV] += uv.x * sd.y + uv.y * sd.x;
+            acc[7 % NV] += pv.x * wd.x - pv.y * wd.y;
+            acc[8 % NV] += pv.x * wd.y + pv.y * wd.x;
+            acc[9 % NV] += pv.x * sd.x - pv.y * sd.y;
+            acc[10 % NV] += pv.x * sd.y + pv.y * sd.x;
           }
         }
       }
@@ -1478,7 +1493,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         if (rv) rv_local.wtrace = (P.trace && trace_it == 20)
                                       ? P.trace + (size_t)P.n_cta * kTraceIters * kTracePhases + (size_t)cta * kTraceStats + 8
                                       : nullptr;
-        if (s_any_refresh) {
+        if (s_any_refresh || P.expand) {
             double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             float facc[22] = {};
             if (!product_step<TM, R, 11>(P, cta, stage_fits, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, s_refresh,
@@ -1567,7 +1582,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     DZ b = {zero, zero}, e = d;
                     if (!s_first[c]) {
                         b = dz_mul(g, dz_of(s_igam4[c]));  // beta = gamma / gamma_old
-                        if (s_refresh[c]) {
+                        if (s_refresh[c] || P.expand) {
                             // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
                             const DZ e12 = {dd_add(so[5 * R + c], so[7 * R + c]), dd_add(so[6 * R + c], so[8 * R + c])};
                             const DZ e3 = {so[9 * R + c], so[10 * R + c]};
@@ -1609,7 +1624,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     br = gr * s_igam_r[c] - gi * s_igam_i[c];
                     bi = gr * s_igam_i[c] + gi * s_igam_r[c];
                     if constexpr (kDFV) s_b4[c] = from_c128<float4>(make_double2(br, bi));
-                    if (s_refresh[c]) {
+                    if (s_refresh[c] || P.expand) {
                         // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
                         const double e12r = s_out[5 * R + c] + s_out[7 * R + c];
                         const double e12i = s_out[6 * R + c] + s_out[8 * R + c];

@@ -28,6 +28,7 @@ FE_PREC_FP64, FE_PREC_MIXED, FE_PREC_DF = 0, 1, 2
 FE_BOUNDARY_ABC, FE_BOUNDARY_SYMMETRY, FE_BOUNDARY_ANTISYMMETRY = 0, 1, 2
 FE_FORMULATION_H, FE_FORMULATION_E = 0, 1
 FE_PRECOND_BLOCK_JACOBI, FE_PRECOND_BICP = 0, 1
+FE_RECURRENCE_CG, FE_RECURRENCE_EXPANDED = 0, 1
 
 LIB_PATH = Path(__file__).resolve().parent / "libfe_gb300.so"
 
@@ -72,7 +73,8 @@ class fe_planewave(C.Structure):
 class fe_solve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("rhs_tile", C.c_int32),
-                ("max_pass_iter", C.c_int32), ("wait_timeout_us", C.c_int32), ("preconditioner", C.c_int32)]
+                ("max_pass_iter", C.c_int32), ("wait_timeout_us", C.c_int32), ("preconditioner", C.c_int32),
+                ("recurrence", C.c_int32)]
 
 
 class fe_solve_stats(C.Structure):
@@ -90,7 +92,7 @@ class fe_serve_opts(C.Structure):
     _fields_ = [("precision", C.c_int32), ("tol", C.c_double), ("reliable", C.c_double),
                 ("max_iter", C.c_int32), ("max_outer", C.c_int32), ("hbm_budget", C.c_int64),
                 ("max_ctas", C.c_int32), ("work_per_cta", C.c_int32), ("max_job_ctas", C.c_int32),
-                ("seg_iters", C.c_int32)]
+                ("seg_iters", C.c_int32), ("recurrence", C.c_int32)]
 
 
 class fe_request(C.Structure):
@@ -399,7 +401,7 @@ def fe_spmv_half(ctx, system, precision: int, nrhs: int, x, y):
 
 def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
                rhs_tile=0, max_pass_iter=None, wait_timeout_us=None,
-               preconditioner=FE_PRECOND_BLOCK_JACOBI) -> fe_solve_opts:
+               preconditioner=FE_PRECOND_BLOCK_JACOBI, recurrence=FE_RECURRENCE_CG) -> fe_solve_opts:
     o = fe_solve_opts()
     load().fe_solve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
@@ -409,6 +411,7 @@ def solve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, m
     if wait_timeout_us is not None:
         o.wait_timeout_us = int(wait_timeout_us)
     o.preconditioner = int(preconditioner)
+    o.recurrence = int(recurrence)
     return o
 
 
@@ -480,7 +483,8 @@ def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_op
 # --------------------------------------------------------------------------
 # Serving
 def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
-               hbm_budget=0, max_ctas=0, work_per_cta=0, max_job_ctas=0, seg_iters=0) -> fe_serve_opts:
+               hbm_budget=0, max_ctas=0, work_per_cta=0, max_job_ctas=0, seg_iters=0,
+               recurrence=FE_RECURRENCE_CG) -> fe_serve_opts:
     o = fe_serve_opts()
     load().fe_serve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
@@ -491,6 +495,7 @@ def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, m
         o.seg_iters = int(seg_iters)
     if work_per_cta:
         o.work_per_cta = int(work_per_cta)
+    o.recurrence = int(recurrence)
     return o
 
 

@@ -363,7 +363,32 @@ def test_mesh_errors(fe, ctx):
 
 
 @pytest.mark.parametrize("precision", ["FP64", "MIXED", "DF"])
-def test_solve_config2_full_size(fe, ctx, config2, precision):
+@pytest.mark.parametrize("name", ["box2", "rand1", "rand2"])
+def test_expanded_recurrence_matches_direct(fe, ctx, name, precision):
+    """FE_RECURRENCE_EXPANDED (p^T A p from its three inner products with the
+    recursive s) solves to the same bar as the default recurrence."""
+    prob = SMALL[name]()
+    waves = W.normal_incidence() if name != "rand2" else W.oblique_wave(0.6, 1.1)
+    maps = fem.mesh_maps(prob)
+    A = fem.assemble(prob, maps=maps)
+    B = fem.rhs(prob, waves, maps=maps)
+    xref = fem.solve_direct(A, B)
+    x, rep = _solve(fe, ctx, prob, waves, getattr(fe, f"FE_PREC_{precision}"), recurrence=fe.FE_RECURRENCE_EXPANDED)
+    res = fem.true_relative_residual(A, x, B)
+    assert rep[0]["status"] == 0
+    assert res.max() <= 1e-8, (res, rep)
+    assert np.linalg.norm(x - xref) <= 1e-6 * np.linalg.norm(xref)
+
+
+def test_unknown_recurrence_is_rejected(fe, ctx):
+    prob = SMALL["box2"]()
+    with pytest.raises(fe.FeError):
+        _solve(fe, ctx, prob, W.normal_incidence(), fe.FE_PREC_DF, recurrence=7)
+
+
+@pytest.mark.parametrize("recurrence", ["CG", "EXPANDED"])
+@pytest.mark.parametrize("precision", ["FP64", "MIXED", "DF"])
+def test_solve_config2_full_size(fe, ctx, config2, precision, recurrence):
     """The 3-wavelength cube at full size (88 998 unknowns) in the launch
     configuration the benchmark times: FP64 true residual <= 1e-8 with the
     oracle's matrix, and relative field error <= 1e-6 against the oracle's
@@ -373,7 +398,8 @@ def test_solve_config2_full_size(fe, ctx, config2, precision):
     ref = np.load(Path(__file__).with_name("golden") / "config2_x.npz")
     xref = ref["x"].astype(np.complex128)
     B = fem.rhs(prob, waves, maps=maps)
-    x, rep = _solve(fe, ctx, prob, waves, getattr(fe, f"FE_PREC_{precision}"))
+    x, rep = _solve(fe, ctx, prob, waves, getattr(fe, f"FE_PREC_{precision}"),
+                    recurrence=getattr(fe, f"FE_RECURRENCE_{recurrence}"))
     res = fem.true_relative_residual(A, x, B)
     assert rep[0]["status"] == 0, rep
     assert res.max() <= 1e-8, (res, rep)
