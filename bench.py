@@ -42,7 +42,7 @@ from pathlib import Path
 ROOT = Path(__file__).resolve().parent
 sys.path.insert(0, str(ROOT))
 
-WORKLOADS = ("config2", "config1", "config3", "config4", "config5", "config2q", "aircraft40")
+WORKLOADS = ("config2", "config1", "config3", "config4", "config5", "config2q", "aircraft40", "config4w1")
 
 
 def parse():
@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--seq-sample", type=int, default=24,
                     help="config5: requests (a seeded random sample) timed through the sequential FP64 path")
     ap.add_argument("--serve-precision", default="df", choices=["df", "fp64", "mixed"])
-    ap.add_argument("--recurrence", default="cg", choices=["cg", "expanded"],
-                    help="COCG step length: Chronopoulos-Gear recurrence or p^T A p from its three inner products")
+    ap.add_argument("--recurrence", default="auto", choices=["auto", "cg", "expanded"],
+                    help="COCG step length: Chronopoulos-Gear recurrence or p^T A p from its three inner products; "
+                         "auto: the library's defaults (cg for solves, expanded for serving)")
     ap.add_argument("--no-poisson", action="store_true",
                     help="config5: skip the Poisson-arrival pass (latency then from the t = 0 pass)")
     ap.add_argument("--serve-only", action="store_true",
@@ -82,7 +83,9 @@ def workload(name):
     return {"config1": W.config1, "config2": W.config2, "config3": W.config3, "config4": W.config4,
             "config2q": W.config2_quarter,
             # the half-size stand-in of the large scatterer: the 40^3 aircraft, its first wave
-            "aircraft40": lambda: (W.aircraft_mesh(40, 4), W.config4()[1].column(0))}[name]()
+            "aircraft40": lambda: (W.aircraft_mesh(40, 4), W.config4()[1].column(0)),
+            # the large scatterer with the first of its 16 waves
+            "config4w1": lambda: (W.aircraft_mesh(80, 4), W.config4()[1].column(0))}[name]()
 
 
 class ClockSampler:
@@ -287,7 +290,8 @@ def run_ours(args, rank, world, local_rank, precision_name):
     ctx = fe.fe_ctx_create(local_rank, stream=stream.cuda_stream)
     opts = fe.solve_opts(precision=precision, tol=1e-8, rhs_tile=args.rhs_tile,
                          preconditioner=fe.FE_PRECOND_BICP if bicp else fe.FE_PRECOND_BLOCK_JACOBI,
-                         recurrence={"cg": fe.FE_RECURRENCE_CG, "expanded": fe.FE_RECURRENCE_EXPANDED}[args.recurrence])
+                         recurrence={"auto": fe.FE_RECURRENCE_CG, "cg": fe.FE_RECURRENCE_CG,
+                                     "expanded": fe.FE_RECURRENCE_EXPANDED}[args.recurrence])
     mat_d = torch.from_numpy(np.ascontiguousarray(prob.material).ravel()).to(f"cuda:{local_rank}")
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local_rank}")
     R = waves.count
@@ -455,7 +459,8 @@ def run_ours(args, rank, world, local_rank, precision_name):
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {prob.name}, {info['n_dof']} unknowns, {R} plane wave(s)",
                    "n_dof": info["n_dof"], "nnzb": info["nnzb"], "rhs": R, "precision": precision_name,
-                   "rhs_tile": args.rhs_tile or "auto", "tile": tile, "recurrence": args.recurrence,
+                   "rhs_tile": args.rhs_tile or "auto", "tile": tile,
+                   "recurrence": "cg" if args.recurrence == "auto" else args.recurrence,
                    "tol": 1e-8, "l2": "512 MiB flush between timed steps", "parallelism": f"replicas x{world}"},
         "converged": ok,
         "iterations_per_solve": inner_iters / (args.steps * R),
@@ -597,7 +602,8 @@ def run_serving(args, rank, world, local_rank):
     reqs = replicas.shard(W.config5(n_requests=args.requests), rank, world)
     ctx = fe.fe_ctx_create(local_rank)
     prec = {"mixed": fe.FE_PREC_MIXED, "fp64": fe.FE_PREC_FP64, "df": fe.FE_PREC_DF}[args.serve_precision]
-    recurrence = {"cg": fe.FE_RECURRENCE_CG, "expanded": fe.FE_RECURRENCE_EXPANDED}[args.recurrence]
+    recurrence = {"auto": fe.FE_RECURRENCE_EXPANDED, "cg": fe.FE_RECURRENCE_CG,
+                  "expanded": fe.FE_RECURRENCE_EXPANDED}[args.recurrence]
     n_solves = sum(q.waves.count for q in reqs)
     n_dof_total = sum(3 * int(np.prod(np.array(q.problem.material.shape) + 1)) for q in reqs)
 
@@ -702,7 +708,8 @@ def run_serving(args, rank, world, local_rank):
         "data": "synthetic",
         "config": {"workload": f"config5: serving stream of {args.requests} cubes 8^3..50^3 nodes, 1-16 plane waves",
                    "requests_per_rank": len(reqs), "rhs_per_rank": n_solves, "grid_dof_per_rank": n_dof_total,
-                   "serve_precision": args.serve_precision, "recurrence": args.recurrence, "tol": 1e-8, "max_job_ctas": args.max_job_ctas or "default",
+                   "serve_precision": args.serve_precision,
+                   "recurrence": "expanded" if args.recurrence == "auto" else args.recurrence, "tol": 1e-8, "max_job_ctas": args.max_job_ctas or "default",
                    "l2": "inputs of successive requests differ; no flush", "parallelism": f"replicas x{world}"},
         "served_ok": ok,
         "served_failed": failed, "served_slowest": [describe(i, res[i]) for i in reversed(slowest)],

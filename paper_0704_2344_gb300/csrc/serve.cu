@@ -384,7 +384,7 @@ void fe_serve_opts_default(fe_serve_opts* o) {
     o->work_per_cta = 2048;
     o->max_job_ctas = 0;
     o->seg_iters = 0;
-    o->recurrence = FE_RECURRENCE_CG;
+    o->recurrence = FE_RECURRENCE_EXPANDED;  // the stream's large requests have long plateaus
 }
 
 int32_t fe_serve_plan(int32_t n, const int64_t* rows, const int32_t* width, int32_t max_ctas, int32_t max_job_ctas,

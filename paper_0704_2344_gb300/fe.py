@@ -484,7 +484,7 @@ def fe_solve_rhs_noalloc(ctx, system, nrhs: int, b_dev, x_dev, opts: fe_solve_op
 # Serving
 def serve_opts(precision=FE_PREC_DF, tol=1e-8, reliable=1e-4, max_iter=100000, max_outer=200,
                hbm_budget=0, max_ctas=0, work_per_cta=0, max_job_ctas=0, seg_iters=0,
-               recurrence=FE_RECURRENCE_CG) -> fe_serve_opts:
+               recurrence=FE_RECURRENCE_EXPANDED) -> fe_serve_opts:
     o = fe_serve_opts()
     load().fe_serve_opts_default(C.byref(o))
     o.precision, o.tol, o.reliable = int(precision), float(tol), float(reliable)
