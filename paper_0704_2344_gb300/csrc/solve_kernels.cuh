@@ -1623,7 +1623,6 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     // beta = gamma / gamma_old
                     br = gr * s_igam_r[c] - gi * s_igam_i[c];
                     bi = gr * s_igam_i[c] + gi * s_igam_r[c];
-                    if constexpr (kDFV) s_b4[c] = from_c128<float4>(make_double2(br, bi));
                     if (s_refresh[c] || P.expand) {
                         // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
                         const double e12r = s_out[5 * R + c] + s_out[7 * R + c];
@@ -1638,8 +1637,6 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                         er = dr - (tr * s_ial_r[c] - ti * s_ial_i[c]);
                         ei = di - (tr * s_ial_i[c] + ti * s_ial_r[c]);
                     }
-                } else if constexpr (kDFV) {
-                    s_b4[c] = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
                 const double ed = er * er + ei * ei;
                 const double gg = gr * gr + gi * gi;
@@ -1657,11 +1654,6 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     const double ar = (gr * er + gi * ei) * ie, ai = (gi * er - gr * ei) * ie;
                     s_al_r[c] = ar;
                     s_al_i[c] = ai;
-                    if constexpr (kDFV) {
-                        const float4 a4 = from_c128<float4>(make_double2(ar, ai));
-                        s_a4[c] = a4;
-                        s_na4[c] = make_float4(-a4.x, -a4.y, -a4.z, -a4.w);
-                    }
                     s_be_r[c] = br;
                     s_be_i[c] = bi;
                     s_gam_r[c] = gr;
