@@ -318,18 +318,19 @@ fe_status fe_spmv_half(fe_ctx* ctx, const fe_system* s, int32_t precision, int32
 /* The form of the COCG step length alpha = gamma / (p^T A p).  Every
  * iteration fuses its inner products into one grid reduction after the
  * product w = A u (u = M r); p^T A p then comes either from the
- * Chronopoulos-Gear recurrence e = delta - beta gamma / alpha_old (one
- * reduction of five values; fastest per iteration), or from three more inner
- * products with the recursively updated s = A p:
- * u^T w + beta (u^T s + p^T w) + beta^2 p^T s (eleven values).  The
- * recurrence subtracts nearly equal quantities on systems whose residual
- * plateaus for thousands of iterations, and there rounding errors in the
- * inner products (FP32 pairs in particular) lengthen the plateau: on the
- * 40^3 voxel aircraft the expanded form halves the FP32-pair iterations
- * (10 645 against 19 385) at about 20 % more time per iteration. */
+ * Chronopoulos-Gear recurrence e = delta - beta gamma / alpha_old (fastest
+ * per iteration), or as u^T w + 2 beta u^T s + beta^2 p^T s with the
+ * recursively updated s = A p (A is symmetric, so p^T A u = u^T s): u^T s and
+ * p^T s are taken in the vector update and summed at the grid barrier that
+ * ends it.  The recurrence subtracts nearly equal quantities on systems whose
+ * residual plateaus for thousands of iterations, and there rounding errors
+ * in the inner products (FP32 pairs in particular) lengthen the plateau: on
+ * the 40^3 voxel aircraft the expanded form roughly halves the FP32-pair
+ * iterations, and the 80^3 aircraft converges only with it.  Solves with the
+ * block incomplete Cholesky preconditioner use the recurrence. */
 typedef enum fe_recurrence {
     FE_RECURRENCE_CG = 0,       /* Chronopoulos-Gear (default) */
-    FE_RECURRENCE_EXPANDED = 1  /* p^T A p from its three inner products */
+    FE_RECURRENCE_EXPANDED = 1  /* p^T A p = u^T w + 2 beta u^T s + beta^2 p^T s */
 } fe_recurrence;
 
 typedef enum fe_preconditioner {

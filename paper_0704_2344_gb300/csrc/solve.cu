@@ -234,7 +234,9 @@ static void fill_params(SolveParams& P, const fe_system* s, const Workspace& w, 
     P.rep_rel = (double*)((char*)w.rep.ptr + ((3 * R * sizeof(int) + 15) / 16) * 16);
     P.timeout_ns = 1000ull * (unsigned long long)(o.wait_timeout_us > 0 ? o.wait_timeout_us : 4000000);
     P.spin_ns = 0;  // barrier waits poll without back-off (measured fastest)
-    P.expand = o.recurrence == FE_RECURRENCE_EXPANDED ? 1 : 0;
+    // the expanded recurrence takes u^T s in the block-Jacobi update; solves
+    // with the block incomplete Cholesky factor keep the recurrence
+    P.expand = o.recurrence == FE_RECURRENCE_EXPANDED && !(o.preconditioner == FE_PRECOND_BICP && fp64) ? 1 : 0;
     if (o.preconditioner == FE_PRECOND_BICP && fp64) {
         P.bicp_l = (const double2*)s->bicp_l.ptr;
         P.bicp_linv = (const double2*)s->bicp_linv.ptr;

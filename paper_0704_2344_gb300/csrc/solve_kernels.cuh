@@ -44,6 +44,7 @@ struct ColState {
     double bn, rr_ref, rel, gam_r, gam_i, al_r, al_i, be_r, be_i, igam_r, igam_i, ial_r, ial_i, pad;
     float4 a4, na4, b4;
     float4 gam4, igam4, ial4;  // FP32-pair solves: gamma, 1/gamma, 1/alpha as pairs
+    long long xd[4];           // expanded recurrence: u^T s and p^T s of the last update (the raw 8-byte slots)
     int active, done, status, iters, outer, first, refresh, repl, pass_it, pad2[3];
 };
 struct JobState {
@@ -135,8 +136,8 @@ struct SolveParams {
     unsigned long long* trace;  // optional [n_cta][kTraceIters][kTracePhases] timestamps
     unsigned long long timeout_ns;
     unsigned spin_ns;           // back-off between polls of the barrier generation
-    int expand;                 // p^T A p of every iteration from its three dots (u^T s, p^T w, p^T s) with the
-                                // recursive s, not from the Chronopoulos-Gear recurrence
+    int expand;                 // p^T A p of every iteration as u^T w + 2 beta u^T s + beta^2 p^T s (u^T s and
+                                // p^T s taken in the update), not from the Chronopoulos-Gear recurrence
     // block incomplete Cholesky factor, one band per CTA (FP64 solves; null:
     // block Jacobi)
     const double2* bicp_l;      // [nnzb * 9] L_IJ by block slot, row-major 3x3
@@ -686,11 +687,6 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             dfc_mac4(facc + 14 % (2 * NV), pv, wy);
             dfc_mac4(facc + 18 % (2 * NV), pv, sy);
             ((float4*)P.s)[o] = sy;
-          } else if (P.expand) {  // the same dots with the recursive s
-            const float4 pv = ld_cg((const float4*)P.p + o), sv = ld_cg((const float4*)P.s + o);
-            dfc_mac4(facc + 10 % (2 * NV), uv, sv);
-            dfc_mac4(facc + 14 % (2 * NV), pv, wy);
-            dfc_mac4(facc + 18 % (2 * NV), pv, sv);
           }
         }
       } else {
@@ -710,14 +706,6 @@ __device__ __forceinline__ bool product_phase(const SolveParams& P, const typena
             acc[9 % NV] += pv.x * sd.x - pv.y * sd.y;
             acc[10 % NV] += pv.x * sd.y + pv.y * sd.x;
             P.s[o] = sd;
-          } else if (P.expand) {  // the same dots with the recursive s
-            const double2 pv = __ldcg(P.p + o), sd = __ldcg(P.s + o);
-            acc[5 % NV] += uv.x * sd.x - uv.y * sd.y;
-            acc[6 % NV] += uv.x * sd.y + uv.y * sd.x;
-            acc[7 % NV] += pv.x * wd.x - pv.y * wd.y;
-            acc[8 % NV] += pv.x * wd.y + pv.y * wd.x;
-            acc[9 % NV] += pv.x * sd.x - pv.y * sd.y;
-            acc[10 % NV] += pv.x * sd.y + pv.y * sd.x;
           }
         }
       }
@@ -1142,6 +1130,10 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
     __shared__ float4 s_gam4[kDFV ? R : 1], s_igam4[kDFV ? R : 1], s_ial4[kDFV ? R : 1];
     __shared__ float s_ibn2f[kDFV ? R : 1], s_irrf[kDFV ? R : 1];
     __shared__ int s_scl_ok[kDFV ? R : 1];
+    // the expanded recurrence: u^T s and p^T s of the last update (u, p, s as
+    // the update left them), summed over the grid at the barrier that ends it
+    // (FP32 pairs in the 8-byte slots for FP32-pair solves)
+    __shared__ double s_xd[4 * R];
     // FP32 forms of 1/||b||^2 and 1/rr_ref, set whenever those change (rare)
     auto set_scales = [&](int c) {
         if constexpr (kDFV) {
@@ -1274,6 +1266,8 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                 s_ial4[tid] = cs.ial4;
                 set_scales(tid);
             }
+#pragma unroll
+            for (int k = 0; k < 4; ++k) s_xd[k * R + tid] = __longlong_as_double(cs.xd[k]);
             s_active[tid] = cs.active;
             s_done[tid] = cs.done;
             s_status[tid] = cs.status;
@@ -1493,7 +1487,7 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         if (rv) rv_local.wtrace = (P.trace && trace_it == 20)
                                       ? P.trace + (size_t)P.n_cta * kTraceIters * kTracePhases + (size_t)cta * kTraceStats + 8
                                       : nullptr;
-        if (s_any_refresh || P.expand) {
+        if (s_any_refresh) {
             double acc[11] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
             float facc[22] = {};
             if (!product_step<TM, R, 11>(P, cta, stage_fits, uM, pr0, pr1, halo_buf, &s_mbar, mbar_phase, s_refresh,
@@ -1582,11 +1576,16 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     DZ b = {zero, zero}, e = d;
                     if (!s_first[c]) {
                         b = dz_mul(g, dz_of(s_igam4[c]));  // beta = gamma / gamma_old
-                        if (s_refresh[c] || P.expand) {
+                        if (s_refresh[c]) {
                             // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
                             const DZ e12 = {dd_add(so[5 * R + c], so[7 * R + c]), dd_add(so[6 * R + c], so[8 * R + c])};
                             const DZ e3 = {so[9 * R + c], so[10 * R + c]};
                             e = dz_add(dz_add(d, dz_mul(b, e12)), dz_mul(dz_mul(b, b), e3));
+                        } else if (P.expand) {
+                            // u^T w + 2 beta u^T s + beta^2 p^T s, u^T s and p^T s from the last update
+                            const float2* sx = (const float2*)s_xd;
+                            const DZ us = {sx[c], sx[R + c]}, ps = {sx[2 * R + c], sx[3 * R + c]};
+                            e = dz_add(dz_add(d, dz_mul(dz_add(b, b), us)), dz_mul(dz_mul(b, b), ps));
                         } else {
                             e = dz_sub(d, dz_mul(dz_mul(b, g), dz_of(s_ial4[c])));  // delta - beta gamma / alpha_old
                         }
@@ -1623,7 +1622,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     // beta = gamma / gamma_old
                     br = gr * s_igam_r[c] - gi * s_igam_i[c];
                     bi = gr * s_igam_i[c] + gi * s_igam_r[c];
-                    if (s_refresh[c] || P.expand) {
+                    if (P.expand && !s_refresh[c]) {
+                        // u^T w + 2 beta u^T s + beta^2 p^T s, u^T s and p^T s from the last update
+                        const double b2r = br * br - bi * bi, b2i = 2.0 * br * bi;
+                        const double usr = s_xd[c], usi = s_xd[R + c], psr = s_xd[2 * R + c], psi = s_xd[3 * R + c];
+                        er = dr + 2.0 * (br * usr - bi * usi) + (b2r * psr - b2i * psi);
+                        ei = di + 2.0 * (br * usi + bi * usr) + (b2r * psi + b2i * psr);
+                    } else if (s_refresh[c]) {
                         // p^T A p for p = u + beta p_old: u^T w + beta (u^T s + p^T w) + beta^2 p^T s
                         const double e12r = s_out[5 * R + c] + s_out[7 * R + c];
                         const double e12i = s_out[6 * R + c] + s_out[8 * R + c];
@@ -1678,6 +1683,12 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
         __syncthreads();
         FE_TRACE_MARK(5);
         // ---- [C] update, one thread per (dof, column) ----
+        // With the expanded recurrence the update also takes u^T s and p^T s of
+        // the new u, p and s: with u^T w from the next product they give the
+        // next p^T A p = u^T w + 2 beta u^T s + beta^2 p^T s (A symmetric, so
+        // p^T A u = u^T A p, here u^T s).
+        float xf[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        double xd[4] = {0.0, 0.0, 0.0, 0.0};
         {
             const bool act = s_active[my_c] != 0 && !s_repl[my_c];
             if (s_active[my_c] && s_repl[my_c])
@@ -1697,10 +1708,10 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     const int i = base + tid;
                     const bool valid = act && tid < kChunk && i < n3;
                     const size_t o = base_o + i;
-                    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f);
+                    float4 rn = make_float4(0.f, 0.f, 0.f, 0.f), pp = rn, ss = rn;
                     if (valid) {
-                        const float4 pp = dfc_axpy(ld_cg(U + o), b4, ld_cg(Pv + o));
-                        const float4 ss = dfc_axpy(ld_cg(wv + o), b4, ld_cg(Sv + o));
+                        pp = dfc_axpy(ld_cg(U + o), b4, ld_cg(Pv + o));
+                        ss = dfc_axpy(ld_cg(wv + o), b4, ld_cg(Sv + o));
                         Pv[o] = pp;
                         Sv[o] = ss;
                         X[o] = dfc_axpy(ld_cg(X + o), a4, pp);
@@ -1716,7 +1727,12 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                         float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
                         for (int be = 0; be < 3; ++be) dfc_mac(acc, __ldg(drow + be), ex[tid + (be - al) * R]);
-                        U[o] = df_result_norm(acc);
+                        const float4 uu = df_result_norm(acc);
+                        U[o] = uu;
+                        if (P.expand) {
+                            dfc_mac4(xf + 0, uu, ss);
+                            dfc_mac4(xf + 4, pp, ss);
+                        }
                     }
                     __syncthreads();
                 }
@@ -1725,10 +1741,10 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                 const int i = base + tid;
                 const bool valid = act && tid < kChunk && i < n3;
                 const size_t o = base_o + i;
-                double2 rn = make_double2(0.0, 0.0);
+                double2 rn = make_double2(0.0, 0.0), pp = rn, ss = rn;
                 if (valid) {
-                    const double2 pp = cfma(beta, __ldcg(P.p + o), __ldcg(P.u + o));
-                    const double2 ss = cfma(beta, __ldcg(P.s + o), to_c128(ld_cg(wv + o)));
+                    pp = cfma(beta, __ldcg(P.p + o), __ldcg(P.u + o));
+                    ss = cfma(beta, __ldcg(P.s + o), to_c128(ld_cg(wv + o)));
                     P.p[o] = pp;
                     P.s[o] = ss;
                     P.x[o] = cfma(alpha, pp, __ldcg(P.x + o));
@@ -1746,6 +1762,12 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
                     for (int be = 0; be < 3; ++be) uu = cfma(__ldg(drow + be), s_exch[tid + (be - al) * R], uu);
                     P.u[o] = uu;
                     if (kSplit) uM[o] = from_c128<C>(uu);
+                    if (P.expand) {
+                        xd[0] += uu.x * ss.x - uu.y * ss.y;
+                        xd[1] += uu.x * ss.y + uu.y * ss.x;
+                        xd[2] += pp.x * ss.x - pp.y * ss.y;
+                        xd[3] += pp.x * ss.y + pp.y * ss.x;
+                    }
                 }
                 __syncthreads();
             }
@@ -1758,7 +1780,13 @@ __device__ __forceinline__ void solve_body(const SolveParams& P, const int cta) 
             }
         }
         FE_TRACE_MARK(6);
-        if (!grid_reduce<0>(P, cta, s_in, s_out)) goto out;
+        if (P.expand) {
+            if constexpr (kDFV) cta_colsum_df<R, 4>(xf, s_red, s_in);
+            else cta_colsum<R, 4>(xd, s_red, s_in);
+            if (!grid_reduce<4 * R, kDFV>(P, cta, s_in, s_xd)) goto out;
+        } else if (!grid_reduce<0>(P, cta, s_in, s_out)) {
+            goto out;
+        }
         FE_TRACE_MARK(7);
         ++trace_it;
         ++seg_it;
@@ -1790,6 +1818,8 @@ out:
                     cs.igam4 = s_igam4[tid];
                     cs.ial4 = s_ial4[tid];
                 }
+#pragma unroll
+                for (int k = 0; k < 4; ++k) cs.xd[k] = __double_as_longlong(s_xd[k * R + tid]);
                 cs.active = s_active[tid];
                 cs.done = s_done[tid];
                 cs.status = s_status[tid];
