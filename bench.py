@@ -397,8 +397,9 @@ def run_ours(args, rank, world, local_rank, precision_name):
     if bicp:
         common["bicp_band_blocks"] = bicp_blocks
         common["bicp_factor_ms"] = round(bicp_factor_ms, 3)
-    # The roofline of the method's own work (the survey's per-product bytes
-    # and flops), not of the arithmetic that implements it.
+    # The roofline of the method's own work (every stored block, the row
+    # pointers and the input and output vectors once per product; 8 flops per
+    # complex multiply-add), not of the arithmetic that implements it.
     s_inner = 8 if base == "mixed" else 16
     steps = args.steps
     pb_inner = product_bytes(info, s_inner, tile_w)

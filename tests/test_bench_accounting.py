@@ -87,7 +87,7 @@ def test_recorded_traffic_follows_the_kernel_sources(bench, monkeypatch):
 
 
 def test_method_bytes_per_product_match_the_worked_figures(bench):
-    # The survey's worked figures for the 3-wavelength cube (748 658 blocks,
+    # Worked figures for the 3-wavelength cube (748 658 blocks,
     # 29 666 nodes, 88 998 unknowns), one column: 58.4 MB per complex64
     # product and 113.8 MB per complex128 (or FP32-pair) product.
     c2 = {"nnzb": 748658, "n_nodes": 29666, "n_dof": 88998}
@@ -107,3 +107,19 @@ def test_method_products_count_the_slowest_column_of_each_launch(bench):
     # one column per launch: a column with two passes has no intermediate refresh
     assert bench.method_products(rep[:1], 1) == (10 + 1, 3)
     assert bench.method_products(rep[1:2], 1) == (12, 2)
+
+
+def test_reference_arm_reports_the_time_it_ran(bench, capsys):
+    """The reference arm times bounded samples of the oracle's solve: its
+    line's rate is the solves those samples did over the time they ran, so
+    rate, solves per step and time per step agree, and the time it claims
+    fits in the time the call took."""
+    import argparse
+    import json
+    args = argparse.Namespace(workload="config2", cpu_sample_s=3.0, steps=2, warmup=0, gpus=1)
+    bench.run_reference(args)
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["value"] == pytest.approx(line["solves_per_step"] * 1e3 / line["ms_per_step"], rel=1e-3)
+    assert line["ms_per_step"] * line["steps"] <= 1e3 * line["wall_s"]
+    assert line["config"]["workload"].startswith("config2: ") and "88998 unknowns" in line["config"]["workload"]
