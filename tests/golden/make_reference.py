@@ -6,9 +6,10 @@ the repository root:  python tests/golden/make_reference.py [config2 config3 air
 Outputs (x as complex64 is enough for a 1e-6 relative field comparison: its
 rounding is ~6e-8 relative):
   tests/golden/config2_x.npz     the 3-wavelength cube, one wave, SuperLU;
-  tests/golden/config3_x.npz     the same mesh with the 64 sphere waves, the
-                                 columns in CONFIG3_COLUMNS (two of each
-                                 32-column launch), SuperLU;
+  tests/golden/config3_x.npz     the same mesh with the 64 sphere waves, SuperLU:
+                                 the columns in CONFIG3_COLUMNS (two of each
+                                 32-column launch) in full, and all 64 on a
+                                 seeded sample of CONFIG3_SAMPLE unknowns;
   tests/golden/aircraft40_x.npz  the 40^3 aircraft with the first of the
                                  large-scatterer waves, the oracle's COCG down
                                  to a true residual of 1e-12 (a direct
@@ -28,6 +29,7 @@ from paper_0704_2344_gb300 import workloads as W  # noqa: E402
 
 HERE = Path(__file__).resolve().parent
 CONFIG3_COLUMNS = (0, 17, 32, 63)
+CONFIG3_SAMPLE = 4096
 
 
 def config2():
@@ -57,8 +59,11 @@ def config3():
     res = fem.true_relative_residual(A, X, B)
     print("config 3: n_dof", maps.n_dof, "solve s", round(time.time() - t, 1), "max residual", res.max())
     cols = np.array(CONFIG3_COLUMNS)
+    # every column on a seeded sample of unknowns, for a per-column field check of all 64
+    rows = np.sort(np.random.default_rng(20070704 + 33).choice(maps.n_dof, size=CONFIG3_SAMPLE, replace=False))
     np.savez_compressed(HERE / "config3_x.npz", x=X[:, cols].astype(np.complex64), columns=cols,
-                        residual=res[cols], n_dof=maps.n_dof)
+                        residual=res[cols], n_dof=maps.n_dof, sample_rows=rows,
+                        x_sample=X[rows, :].astype(np.complex64), residual_all=res)
 
 
 def aircraft40():
